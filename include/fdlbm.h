@@ -1,0 +1,170 @@
+/*
+ * fdlbm.h -- C ABI of the GB300 (sm_103a) FD-LBM / MRT D2Q9 library.
+ *
+ * The schemes are those of Dubois, Lallemand, Obrecht, Tekitek, "Lattice
+ * Boltzmann model approximated with finite difference expressions"
+ * (Computers & Fluids 155, 2017):
+ *   - FD-LBM (Sec. 2): only the primitive moments (rho, ux, uy) are kept per
+ *     node.  Each step rebuilds the 9 populations at every node from the
+ *     equilibria of Sec. 1-a plus (1 - 1/s) theta (Eq. order2), with the
+ *     defects theta_E, theta_XX, theta_XY estimated by three- or five-point
+ *     finite differences, maps them to populations with M^-1 (Sec. 1) and
+ *     propagates them one link (Eq. 2).
+ *   - MRT D2Q9 (Sec. 1, 1-a): collision of the non-conserved moments towards
+ *     their equilibria (Eq. 1) and propagation (Eq. 2).
+ *   - Body force: Strang splitting, half before and half after the
+ *     collision (Sec. 1).  Walls (Sec. 3-b, 3-c): FD-LBM extrapolates the
+ *     velocity linearly to zero at walls placed xi outside the first and
+ *     last fluid rows; MRT uses half-way bounce-back (xi = 1/2).
+ *
+ * Conventions shared by all entry points
+ *   - Fields are row-major [ny][nx], node (i, j) at j*nx + i, i along x.
+ *   - Density is passed as the deviation drho = rho - 1, so that FP32 keeps
+ *     the resolution of small perturbations.  Velocities are u = (J + F/2) /
+ *     rho, the physical velocity at the middle of the force splitting.
+ *   - Device pointers are CUDA device (or managed) pointers on the device
+ *     that was current at fdlbm_create.  Host pointers are ordinary host
+ *     memory; pinned memory makes the copies asynchronous.
+ *   - Every call is enqueued on the stream given at creation (or set with
+ *     fdlbm_set_stream) and returns without waiting, except fdlbm_reduce,
+ *     the *_host variants and fdlbm_sync, which wait for the stream.
+ *   - The caller owns the workspace and every buffer.  The library owns only
+ *     the small host-side handle; it never calls cudaMalloc or cudaFree.
+ *   - Errors: every int-returning call returns FDLBM_OK (0) or a negative
+ *     fdlbm_status.  Nothing aborts or throws.  The text of the last error on
+ *     a handle is available from fdlbm_last_error.  Errors found on the
+ *     device (a non-finite velocity, see fdlbm_check) are reported by the
+ *     next call that waits for the stream.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef FDLBM_H
+#define FDLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FDLBM_OK 0
+#define FDLBM_ERR_INVALID (-1)     /* bad argument or parameter            */
+#define FDLBM_ERR_UNSUPPORTED (-2) /* valid but not implemented combination */
+#define FDLBM_ERR_NOMEM (-3)       /* workspace too small                   */
+#define FDLBM_ERR_CUDA (-4)        /* a CUDA runtime call failed            */
+#define FDLBM_ERR_DIVERGED (-5)    /* non-finite values found on the device */
+#define FDLBM_ERR_TIMEOUT (-6)     /* a bounded device-side wait expired    */
+
+/* ---- scheme, boundary, storage ----------------------------------------- */
+#define FDLBM_SCHEME_FD3 3   /* FD-LBM, three-point differences (Sec. 2)   */
+#define FDLBM_SCHEME_FD5 5   /* FD-LBM, five-point differences (Sec. 2)    */
+#define FDLBM_SCHEME_MRT 100 /* multiple-relaxation-time D2Q9 (Sec. 1-a)  */
+
+#define FDLBM_BOUNDARY_PERIODIC 0 /* periodic in x and y                  */
+#define FDLBM_BOUNDARY_WALLS_Y 1  /* periodic in x; walls below row 0 and
+                                     above row ny-1 (channel, Sec. 3-c)    */
+
+#define FDLBM_STORAGE_F32 0  /* state stored in FP32                      */
+#define FDLBM_STORAGE_F16 1  /* FD-LBM only: (rho-1, ux, uy) in FP16, FP32 math */
+#define FDLBM_STORAGE_BF16 2 /* FD-LBM only: (rho-1, ux, uy) in BF16, FP32 math */
+
+/* Parameters of one lattice.  Relaxation rates lie in (0, 2).
+ *   s_xx : rate of XX and XY; shear viscosity nu = (1/s_xx - 1/2)/3 (Sec. 1-a)
+ *   s_e  : rate of E; bulk viscosity zeta = (1/s_e - 1/2)/3 (Sec. 1-a)
+ *   s_q  : rate of qx, qy (MRT only; FD-LBM sets q = -J, Sec. 2)
+ *   s_eps: rate of epsilon (MRT only; FD-LBM sets epsilon to equilibrium)
+ *   wall_xi: walls at y = -xi and y = ny-1+xi in lattice units, 0 < xi <= 1
+ *            (FD-LBM); MRT requires xi = 1/2.  Ignored when periodic.
+ *   force_x, force_y: uniform body force per node and time step. */
+typedef struct fdlbm_params {
+    int32_t nx, ny;
+    int32_t scheme;   /* FDLBM_SCHEME_*   */
+    int32_t boundary; /* FDLBM_BOUNDARY_* */
+    int32_t storage;  /* FDLBM_STORAGE_*  */
+    int32_t flags;    /* reserved, must be 0 */
+    double s_xx, s_e, s_q, s_eps;
+    double wall_xi;
+    double force_x, force_y;
+} fdlbm_params;
+
+typedef struct fdlbm_s fdlbm_t;
+
+/* Bytes of device workspace that fdlbm_create needs for these parameters:
+ * two copies of the state (ping-pong), a staging area for host transfers
+ * and reduction scratch.  Returns 0 if the parameters are invalid. */
+size_t fdlbm_workspace_size(const fdlbm_params* params);
+
+/* Create a handle on the current CUDA device.  workspace: device memory of
+ * at least fdlbm_workspace_size bytes, 256-byte aligned, owned by the caller
+ * and kept alive until fdlbm_destroy.  stream: a cudaStream_t (NULL = the
+ * legacy default stream).  On success *out receives the handle.  The state
+ * is undefined until fdlbm_init* is called. */
+int fdlbm_create(const fdlbm_params* params, void* workspace, size_t workspace_bytes,
+                 void* stream, fdlbm_t** out);
+
+/* Release the host-side handle.  Never touches the workspace. */
+void fdlbm_destroy(fdlbm_t* h);
+
+/* Change the stream that later calls are enqueued on. */
+int fdlbm_set_stream(fdlbm_t* h, void* stream);
+
+/* Load the initial state from device arrays drho, ux, uy (nx*ny floats
+ * each, row-major).  For MRT the populations are set to the equilibria of
+ * Sec. 1-a at (rho, J = rho u - F/2), so the reported velocity is u. */
+int fdlbm_init(fdlbm_t* h, const float* drho, const float* ux, const float* uy);
+
+/* Same, from host arrays (copied through the workspace staging area; waits
+ * for the copies to finish before returning). */
+int fdlbm_init_host(fdlbm_t* h, const float* drho, const float* ux, const float* uy);
+
+/* Initial state rho = 1 and u = V + sum of transverse plane waves
+ * A cos(k.x + phase) (-ky, kx)/|k| with k = 2 pi (m / nx, n / ny)
+ * (shear waves, Sec. 3-a), evaluated on the device.  modes: host array of
+ * n_modes records {m, n, A, phase} (4 doubles each). */
+int fdlbm_init_modes(fdlbm_t* h, int32_t n_modes, const double* modes, double mean_ux,
+                     double mean_uy);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  nsteps = 0 is a no-op. */
+int fdlbm_step(fdlbm_t* h, int64_t nsteps);
+
+/* Write the current drho, ux, uy into device arrays (nx*ny floats each). */
+int fdlbm_moments(fdlbm_t* h, float* drho, float* ux, float* uy);
+
+/* Same into host arrays; waits for the copies. */
+int fdlbm_moments_host(fdlbm_t* h, float* drho, float* ux, float* uy);
+
+/* FP64 reductions over the lattice, computed on the device and returned in
+ * the host array out (waits for the stream):
+ *   FDLBM_REDUCE_MASS     out[0] = sum drho
+ *   FDLBM_REDUCE_MOMENTUM out[0..1] = sum rho ux, sum rho uy
+ *   FDLBM_REDUCE_ENERGY   out[0] = sum rho |u|^2 / 2
+ *   FDLBM_REDUCE_MODE     args[0..1] = (m, n); out[0..1] = real and imaginary
+ *                         parts of (1/(nx ny)) sum u_t exp(-i k.x), u_t the
+ *                         velocity component along (-ky, kx)/|k|: the
+ *                         correlation A(t) of Sec. 3-a (A/2 e^{i phase} for
+ *                         one wave of amplitude A)
+ *   FDLBM_REDUCE_MAXABS   out[0] = max |u|, out[1] = max |drho|
+ * A non-finite value anywhere makes the call return FDLBM_ERR_DIVERGED. */
+#define FDLBM_REDUCE_MASS 0
+#define FDLBM_REDUCE_MOMENTUM 1
+#define FDLBM_REDUCE_ENERGY 2
+#define FDLBM_REDUCE_MODE 3
+#define FDLBM_REDUCE_MAXABS 4
+int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out);
+
+/* Wait for all work enqueued by this handle. */
+int fdlbm_sync(fdlbm_t* h);
+
+/* Text of the last error on this handle ("" if none); valid until the next
+ * call on the handle.  fdlbm_status_string maps a status code to its name. */
+const char* fdlbm_last_error(const fdlbm_t* h);
+const char* fdlbm_status_string(int status);
+
+/* Number of kernel launches this handle has enqueued since creation. */
+int64_t fdlbm_launch_count(const fdlbm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDLBM_H */

@@ -1,0 +1,337 @@
+// aux_kernels.cu -- initialisation, moment extraction and FP64 reductions.
+#include "mrt_common.cuh"
+
+namespace fdlbm {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---- FD-LBM: contiguous FP32 (rho-1, ux, uy) -> stored state ---------------
+
+template <typename T>
+__global__ void fd_init_kernel(const float* __restrict__ drho, const float* __restrict__ ux,
+                               const float* __restrict__ uy, T* __restrict__ dst, int nx, int ny,
+                               size_t pitch, size_t plane) {
+    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const size_t i = (size_t)y * nx + x, o = (size_t)y * pitch + x;
+    Storage<T>::store(dst + o, drho[i]);
+    Storage<T>::store(dst + plane + o, ux[i]);
+    Storage<T>::store(dst + 2 * plane + o, uy[i]);
+}
+
+// ---- MRT: equilibrium start --------------------------------------------------
+
+// Deviation populations h^eq_a at node n for (rho-1, u): the equilibria of
+// Sec. 1-a at J = rho u - F/2 (so that the reported velocity is u).
+__device__ __forceinline__ void mrt_eq_node(const float* drho, const float* ux, const float* uy,
+                                            size_t n, const MrtCoeffs& c, float g[9]) {
+    const float dr = drho[n];
+    const float jx = fmaf(dr, ux[n], ux[n]) - 0.5f * c.fx;
+    const float jy = fmaf(dr, uy[n], uy[n]) - 0.5f * c.fy;
+    float e, xx, xy, ep;
+    mrt_equilibrium(dr, jx, jy, &e, &xx, &xy, &ep);
+    moments_to_populations(dr, jx, jy, e, xx, xy, -jx, -jy, ep, g);
+}
+
+// Pull layout: stored h_b(y) must be what the next step pulls, so that the
+// first step sees f^0 = f^eq everywhere: h_b(y) = h^eq_b(y + c_b) when
+// y + c_b is fluid, otherwise (bounce-back link) h^eq_opp(b)(y).
+template <bool WALLS>
+__global__ void mrt_init_kernel(const float* __restrict__ drho, const float* __restrict__ ux,
+                                const float* __restrict__ uy, float* __restrict__ dst, int nx,
+                                int ny, size_t pitch, size_t plane, MrtCoeffs c) {
+    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const int cx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int cy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    float own[9];
+    mrt_eq_node(drho, ux, uy, (size_t)y * nx + x, c, own);
+    for (int b = 0; b < 9; ++b) {
+        const int xd = wrap_index(x + cx[b], nx);
+        int yd = y + cy[b];
+        float v;
+        if (WALLS && (yd < 0 || yd >= ny)) {
+            v = own[opp[b]];
+        } else {
+            yd = wrap_index(yd, ny);
+            float g[9];
+            mrt_eq_node(drho, ux, uy, (size_t)yd * nx + xd, c, g);
+            v = g[b];
+        }
+        dst[b * plane + (size_t)y * pitch + x] = v;
+    }
+}
+
+// ---- transverse plane waves (shear waves / Stokes modes) ---------------------
+
+struct ModeList {
+    int n;
+    double mean_ux, mean_uy;
+    double rec[kMaxModes][4];  // m, n, amplitude, phase
+};
+
+__global__ void modes_kernel(ModeList ml, int nx, int ny, float* __restrict__ drho,
+                             float* __restrict__ ux, float* __restrict__ uy) {
+    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    double vx = ml.mean_ux, vy = ml.mean_uy;
+    for (int k = 0; k < ml.n; ++k) {
+        const double kx = 2.0 * M_PI * ml.rec[k][0] / nx, ky = 2.0 * M_PI * ml.rec[k][1] / ny;
+        const double kk = sqrt(kx * kx + ky * ky);
+        const double w = ml.rec[k][2] * cos(kx * x + ky * y + ml.rec[k][3]);
+        vx += -w * ky / kk;
+        vy += w * kx / kk;
+    }
+    const size_t i = (size_t)y * nx + x;
+    drho[i] = 0.f;
+    ux[i] = (float)vx;
+    uy[i] = (float)vy;
+}
+
+// ---- moments ---------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void fd_node(const T* s, size_t plane, size_t o, float* dr,
+                                        float* ux, float* uy) {
+    *dr = Storage<T>::load(s + o);
+    *ux = Storage<T>::load(s + plane + o);
+    *uy = Storage<T>::load(s + 2 * plane + o);
+}
+
+template <bool WALLS>
+__device__ __forceinline__ void mrt_node(const float* s, int x, int y, int nx, int ny,
+                                         size_t pitch, size_t plane, float fx, float fy,
+                                         float* dr, float* ux, float* uy) {
+    float f[9], m[9];
+    mrt_pull<WALLS>(s, x, y, nx, ny, pitch, plane, f);
+    populations_to_moments(f, m);
+    const float inv = __frcp_rn(1.f + m[0]);
+    const float px = m[1] + 0.5f * fx, py = m[2] + 0.5f * fy;
+    *dr = m[0];
+    *ux = fmaf(-px * m[0], inv, px);
+    *uy = fmaf(-py * m[0], inv, py);
+}
+
+template <typename T, int KIND>  // KIND 0: FD-LBM, 1: MRT periodic, 2: MRT walls
+__device__ __forceinline__ void node_state(const void* s, int x, int y, int nx, int ny,
+                                           size_t pitch, size_t plane, float fx, float fy,
+                                           float* dr, float* ux, float* uy) {
+    if (KIND == 0)
+        fd_node(static_cast<const T*>(s), plane, (size_t)y * pitch + x, dr, ux, uy);
+    else
+        mrt_node<KIND == 2>(static_cast<const float*>(s), x, y, nx, ny, pitch, plane, fx, fy,
+                            dr, ux, uy);
+}
+
+template <typename T, int KIND>
+__global__ void moments_kernel(const void* s, int nx, int ny, size_t pitch, size_t plane,
+                               float fx, float fy, float* __restrict__ drho,
+                               float* __restrict__ ux, float* __restrict__ uy) {
+    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    float dr, vx, vy;
+    node_state<T, KIND>(s, x, y, nx, ny, pitch, plane, fx, fy, &dr, &vx, &vy);
+    const size_t i = (size_t)y * nx + x;
+    drho[i] = dr;
+    ux[i] = vx;
+    uy[i] = vy;
+}
+
+// ---- FP64 reductions ----------------------------------------------------------------
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// slot 3 counts non-finite nodes in every reduction
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads)
+    reduce_kernel(const void* s, int nx, int ny, size_t pitch, size_t plane, float fx, float fy,
+                  int what, double a0, double a1, double* __restrict__ partial) {
+    double acc[kReduceSlots] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t total = (int64_t)nx * ny;
+    double kx = 0.0, ky = 0.0, tx = 0.0, ty = 0.0;
+    if (what == FDLBM_REDUCE_MODE) {
+        kx = 2.0 * M_PI * a0 / nx;
+        ky = 2.0 * M_PI * a1 / ny;
+        const double kk = sqrt(kx * kx + ky * ky);
+        tx = kk > 0.0 ? -ky / kk : 0.0;
+        ty = kk > 0.0 ? kx / kk : 0.0;
+    }
+    for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < total;
+         n += (int64_t)gridDim.x * kThreads) {
+        const int x = (int)(n % nx), y = (int)(n / nx);
+        float dr, ux, uy;
+        node_state<T, KIND>(s, x, y, nx, ny, pitch, plane, fx, fy, &dr, &ux, &uy);
+        if (!(isfinite(dr) && isfinite(ux) && isfinite(uy))) {
+            acc[3] += 1.0;
+            continue;
+        }
+        const double rho = 1.0 + (double)dr;
+        switch (what) {
+            case FDLBM_REDUCE_MASS: acc[0] += (double)dr; break;
+            case FDLBM_REDUCE_MOMENTUM:
+                acc[0] += rho * ux;
+                acc[1] += rho * uy;
+                break;
+            case FDLBM_REDUCE_ENERGY:
+                acc[0] += 0.5 * rho * ((double)ux * ux + (double)uy * uy);
+                break;
+            case FDLBM_REDUCE_MODE: {
+                const double ut = tx * ux + ty * uy;
+                double sn, cs;
+                sincos(kx * x + ky * y, &sn, &cs);
+                acc[0] += ut * cs;
+                acc[1] -= ut * sn;
+                break;
+            }
+            default:
+                acc[0] = fmax(acc[0], sqrt((double)ux * ux + (double)uy * uy));
+                acc[1] = fmax(acc[1], fabs((double)dr));
+        }
+    }
+    __shared__ double sh[kThreads / 32][kReduceSlots];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < kReduceSlots; ++k) {
+        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+        const double v = is_max ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kReduceSlots) {
+        const int k = threadIdx.x;
+        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+        double v = sh[0][k];
+        for (int w = 1; w < kThreads / 32; ++w) v = is_max ? fmax(v, sh[w][k]) : v + sh[w][k];
+        partial[blockIdx.x * kReduceSlots + k] = v;
+    }
+}
+
+__global__ void reduce_final_kernel(const double* __restrict__ partial, int nblocks, int what,
+                                    double* __restrict__ result) {
+    const int k = threadIdx.x;
+    if (k >= kReduceSlots) return;
+    const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+    double v = is_max ? 0.0 : 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double p = partial[b * kReduceSlots + k];
+        v = is_max ? fmax(v, p) : v + p;
+    }
+    result[k] = v;
+}
+
+template <typename F>
+cudaError_t dispatch_kind(fdlbm_s* h, F&& f) {
+    if (h->p.scheme == FDLBM_SCHEME_MRT) {
+        if (h->p.boundary == FDLBM_BOUNDARY_WALLS_Y) return f.template run<float, 2>();
+        return f.template run<float, 1>();
+    }
+    switch (h->p.storage) {
+        case FDLBM_STORAGE_F16: return f.template run<__half, 0>();
+        case FDLBM_STORAGE_BF16: return f.template run<__nv_bfloat16, 0>();
+        default: return f.template run<float, 0>();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
+                           void* dst) {
+    dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
+    switch (h->p.storage) {
+        case FDLBM_STORAGE_F16:
+            fd_init_kernel<__half><<<grid, kThreads, 0, h->stream>>>(
+                drho, ux, uy, static_cast<__half*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane);
+            break;
+        case FDLBM_STORAGE_BF16:
+            fd_init_kernel<__nv_bfloat16><<<grid, kThreads, 0, h->stream>>>(
+                drho, ux, uy, static_cast<__nv_bfloat16*>(dst), h->p.nx, h->p.ny, h->L.pitch,
+                h->L.plane);
+            break;
+        default:
+            fd_init_kernel<float><<<grid, kThreads, 0, h->stream>>>(
+                drho, ux, uy, static_cast<float*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mrt_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
+                            void* dst) {
+    dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
+    const MrtCoeffs c = mrt_coeffs(h->p);
+    if (h->p.boundary == FDLBM_BOUNDARY_WALLS_Y)
+        mrt_init_kernel<true><<<grid, kThreads, 0, h->stream>>>(
+            drho, ux, uy, static_cast<float*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane, c);
+    else
+        mrt_init_kernel<false><<<grid, kThreads, 0, h->stream>>>(
+            drho, ux, uy, static_cast<float*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modes_eval(fdlbm_s* h, int n_modes, const double* modes_host, double mean_ux,
+                              double mean_uy, float* drho, float* ux, float* uy) {
+    ModeList ml;
+    ml.n = n_modes;
+    ml.mean_ux = mean_ux;
+    ml.mean_uy = mean_uy;
+    for (int k = 0; k < n_modes; ++k)
+        for (int j = 0; j < 4; ++j) ml.rec[k][j] = modes_host[4 * k + j];
+    dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
+    modes_kernel<<<grid, kThreads, 0, h->stream>>>(ml, h->p.nx, h->p.ny, drho, ux, uy);
+    return cudaGetLastError();
+}
+
+namespace {
+struct MomentsLaunch {
+    fdlbm_s* h;
+    const void* s;
+    float *dr, *ux, *uy;
+    template <typename T, int KIND>
+    cudaError_t run() {
+        dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
+        moments_kernel<T, KIND><<<grid, kThreads, 0, h->stream>>>(
+            s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
+            (float)h->p.force_y, dr, ux, uy);
+        return cudaGetLastError();
+    }
+};
+
+struct ReduceLaunch {
+    fdlbm_s* h;
+    const void* s;
+    int what;
+    double a0, a1;
+    double* partial;
+    template <typename T, int KIND>
+    cudaError_t run() {
+        reduce_kernel<T, KIND><<<kReduceBlocks, kThreads, 0, h->stream>>>(
+            s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
+            (float)h->p.force_y, what, a0, a1, partial);
+        return cudaGetLastError();
+    }
+};
+}  // namespace
+
+cudaError_t launch_moments(fdlbm_s* h, const void* state, float* drho, float* ux, float* uy) {
+    MomentsLaunch ml{h, state, drho, ux, uy};
+    return dispatch_kind(h, ml);
+}
+
+cudaError_t launch_reduce(fdlbm_s* h, const void* state, int what, double a0, double a1,
+                          double* partial, double* result) {
+    ReduceLaunch rl{h, state, what, a0, a1, partial};
+    cudaError_t e = dispatch_kind(h, rl);
+    if (e != cudaSuccess) return e;
+    reduce_final_kernel<<<1, 32, 0, h->stream>>>(partial, kReduceBlocks, what, result);
+    return cudaGetLastError();
+}
+
+}  // namespace fdlbm

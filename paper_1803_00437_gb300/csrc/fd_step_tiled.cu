@@ -1,0 +1,138 @@
+// fd_step_tiled.cu -- general FD-LBM step kernel (Sec. 2, Eq. 2): 2-D tiles
+// staged in shared memory with a halo of r + 1 nodes.  Handles periodic and
+// channel (walls in y) lattices of any size and FP32 / FP16 / BF16 storage.
+//
+// Per CTA (TX x TY outputs):
+//   1. load (rho-1, u) of the tile plus a halo of H = r + 1 nodes (gradients
+//      are needed at the upstream nodes, one link away), and form J = rho u
+//      and the momentum flux J J / rho;
+//   2. at every node of the tile plus a one-node ring, estimate the ten
+//      derivatives, form theta, the reconstructed moments and the 9
+//      populations g_a = f*_a - w_a (kept in shared memory);
+//   3. every output node gathers g_a(x - c_a) (propagation, Eq. 2), closes
+//      rho and u and stores them.
+#include "fd_common.cuh"
+
+namespace fdlbm {
+namespace {
+
+constexpr int kTX = 32, kTY = 16, kThreads = 256;
+
+template <int R, bool WALLS, typename T>
+__global__ void __launch_bounds__(kThreads)
+    fd_step_tiled_kernel(FdState<T> src, FdState<T> dst, int nx, int ny, size_t pitch,
+                         FdCoeffs c) {
+    constexpr int H = R + 1;
+    constexpr int LX = kTX + 2 * H, LY = kTY + 2 * H, LN = LX * LY;
+    constexpr int GX = kTX + 2, GY = kTY + 2, GN = GX * GY;
+    // rho-1, ux, uy, Jx, Jy, Jx Jx/rho, Jx Jy/rho, Jy Jy/rho
+    __shared__ float sf[8][LN];
+    __shared__ float sg[9][GN];
+
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+
+    for (int t = threadIdx.x; t < LN; t += kThreads) {
+        const int lx = t % LX, ly = t / LX;
+        const int x = wrap_index(x0 - H + lx, nx);
+        const int y = y0 - H + ly;
+        float dr, ux, uy;
+        fd_load_node<WALLS>(src, x, y, ny, pitch, c.xi, &dr, &ux, &uy);
+        const float Jx = fmaf(dr, ux, ux), Jy = fmaf(dr, uy, uy);
+        sf[0][t] = dr;
+        sf[1][t] = ux;
+        sf[2][t] = uy;
+        sf[3][t] = Jx;
+        sf[4][t] = Jy;
+        sf[5][t] = Jx * ux;
+        sf[6][t] = Jx * uy;
+        sf[7][t] = Jy * uy;
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < GN; t += kThreads) {
+        const int gx = t % GX, gy = t / GX;
+        const int l = (gy + H - 1) * LX + (gx + H - 1);
+        NodeDerivs d;
+        d.drx = fd_deriv<R>(&sf[0][l], 1);
+        d.dry = fd_deriv<R>(&sf[0][l], LX);
+        d.dJx_x = fd_deriv<R>(&sf[3][l], 1);
+        d.dJx_y = fd_deriv<R>(&sf[3][l], LX);
+        d.dJy_x = fd_deriv<R>(&sf[4][l], 1);
+        d.dJy_y = fd_deriv<R>(&sf[4][l], LX);
+        d.dPxx_x = fd_deriv<R>(&sf[5][l], 1);
+        d.dPxy_x = fd_deriv<R>(&sf[6][l], 1);
+        d.dPxy_y = fd_deriv<R>(&sf[6][l], LX);
+        d.dPyy_y = fd_deriv<R>(&sf[7][l], LX);
+        float g[9];
+        fd_reconstruct(sf[0][l], sf[1][l], sf[2][l], d, c, g);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) sg[a][t] = g[a];
+    }
+    __syncthreads();
+
+    for (int t = threadIdx.x; t < kTX * kTY; t += kThreads) {
+        const int ox = t % kTX, oy = t / kTX;
+        const int x = x0 + ox, y = y0 + oy;
+        if (x >= nx || y >= ny) continue;
+        const int b = (oy + 1) * GX + (ox + 1);
+        float p[9];
+        p[0] = sg[0][b];
+        p[1] = sg[1][b - 1];        // from (x-1, y)
+        p[2] = sg[2][b - GX];       // from (x, y-1)
+        p[3] = sg[3][b + 1];        // from (x+1, y)
+        p[4] = sg[4][b + GX];       // from (x, y+1)
+        p[5] = sg[5][b - GX - 1];   // from (x-1, y-1)
+        p[6] = sg[6][b - GX + 1];   // from (x+1, y-1)
+        p[7] = sg[7][b + GX + 1];   // from (x+1, y+1)
+        p[8] = sg[8][b + GX - 1];   // from (x-1, y+1)
+        float dr, ux, uy;
+        fd_close(p, c, &dr, &ux, &uy);
+        const size_t o = (size_t)y * pitch + x;
+        Storage<T>::store(dst.drho + o, dr);
+        Storage<T>::store(dst.ux + o, ux);
+        Storage<T>::store(dst.uy + o, uy);
+    }
+}
+
+template <int R, bool WALLS, typename T>
+cudaError_t launch_typed(fdlbm_s* h, const void* src, void* dst) {
+    const size_t plane = h->L.plane;
+    const T* s = static_cast<const T*>(src);
+    T* d = static_cast<T*>(dst);
+    FdState<T> S{const_cast<T*>(s), const_cast<T*>(s + plane), const_cast<T*>(s + 2 * plane)};
+    FdState<T> D{d, d + plane, d + 2 * plane};
+    FdCoeffs c;
+    c.a_e = (float)(1.0 - 1.0 / h->p.s_e);
+    c.a_xx = (float)(1.0 - 1.0 / h->p.s_xx);
+    c.fx = (float)h->p.force_x;
+    c.fy = (float)h->p.force_y;
+    c.xi = (float)h->p.wall_xi;
+    dim3 grid((h->p.nx + kTX - 1) / kTX, (h->p.ny + kTY - 1) / kTY);
+    fd_step_tiled_kernel<R, WALLS, T>
+        <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c);
+    return cudaGetLastError();
+}
+
+template <int R, typename T>
+cudaError_t launch_boundary(fdlbm_s* h, const void* src, void* dst) {
+    if (h->p.boundary == FDLBM_BOUNDARY_WALLS_Y) return launch_typed<R, true, T>(h, src, dst);
+    return launch_typed<R, false, T>(h, src, dst);
+}
+
+template <typename T>
+cudaError_t launch_stencil(fdlbm_s* h, const void* src, void* dst) {
+    if (h->p.scheme == FDLBM_SCHEME_FD3) return launch_boundary<1, T>(h, src, dst);
+    return launch_boundary<2, T>(h, src, dst);
+}
+
+}  // namespace
+
+cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst) {
+    switch (h->p.storage) {
+        case FDLBM_STORAGE_F16: return launch_stencil<__half>(h, src, dst);
+        case FDLBM_STORAGE_BF16: return launch_stencil<__nv_bfloat16>(h, src, dst);
+        default: return launch_stencil<float>(h, src, dst);
+    }
+}
+
+}  // namespace fdlbm

@@ -1,0 +1,126 @@
+// fdlbm_internal.cuh -- shared definitions of the CUDA library (not public).
+//
+// D2Q9 velocity set, in the order of the moment matrix of Sec. 1:
+//   c = (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1).
+// The state is held as deviations from the fluid at rest (rho = 1, u = 0):
+// FD-LBM keeps (rho - 1, ux, uy); MRT keeps h_a = f_a - w_a.  With FP32
+// storage this keeps the resolution of small perturbations.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdlbm.h"
+
+namespace fdlbm {
+
+// ---- storage types --------------------------------------------------------
+
+template <typename T>
+struct Storage;
+
+template <>
+struct Storage<float> {
+    static __device__ __forceinline__ float load(const float* p) { return *p; }
+    static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+};
+
+template <>
+struct Storage<__half> {
+    static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+template <>
+struct Storage<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p) {
+        return __bfloat162float(*p);
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) {
+        *p = __float2bfloat16_rn(v);
+    }
+};
+
+// ---- lattice ----------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int wrap_index(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Arguments of the FD-LBM step.  Planes are [ny][pitch] elements.
+template <typename T>
+struct FdState {
+    T* drho;
+    T* ux;
+    T* uy;
+};
+
+struct FdCoeffs {
+    float a_e;    // 1 - 1/s_e  (factor of theta_E)
+    float a_xx;   // 1 - 1/s_xx (factor of theta_XX, theta_XY)
+    float fx, fy; // body force
+    float xi;     // wall offset
+};
+
+struct MrtCoeffs {
+    float s_e, s_xx, s_q, s_eps;
+    float fx, fy;
+};
+
+// ---- handle -------------------------------------------------------------------
+
+struct Layout {
+    size_t pitch;        // elements per stored row (multiple of 64)
+    size_t plane;        // pitch * ny elements
+    size_t elem;         // bytes per stored element
+    int nplanes;         // 3 (FD-LBM) or 9 (MRT)
+    size_t state_bytes;  // one copy of the state
+    size_t off_state[2];
+    size_t off_staging;  // 3 * nx * ny floats
+    size_t off_reduce;   // reduction scratch (doubles)
+    size_t reduce_bytes;
+    size_t off_flag;     // device status word
+    size_t total;
+};
+
+constexpr int kReduceBlocks = 608;  // 4 x 152 SMs
+constexpr int kReduceSlots = 4;     // doubles per block partial
+
+bool compute_layout(const fdlbm_params& p, Layout* L);
+
+}  // namespace fdlbm
+
+struct fdlbm_s {
+    fdlbm_params p;
+    fdlbm::Layout L;
+    cudaStream_t stream;
+    int device;
+    char* ws;
+    int cur;  // index of the current state copy
+    int64_t launches;
+    char err[512];
+};
+
+namespace fdlbm {
+
+MrtCoeffs mrt_coeffs(const fdlbm_params& p);
+
+// launchers (each returns cudaGetLastError() of its launch)
+cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst);
+cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst);
+cudaError_t launch_mrt_step(fdlbm_s* h, const void* src, void* dst);
+cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
+                           void* dst);
+cudaError_t launch_mrt_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
+                            void* dst);
+constexpr int kMaxModes = 64;
+cudaError_t launch_modes_eval(fdlbm_s* h, int n_modes, const double* modes_host, double mean_ux,
+                              double mean_uy, float* drho, float* ux, float* uy);
+cudaError_t launch_moments(fdlbm_s* h, const void* state, float* drho, float* ux, float* uy);
+cudaError_t launch_reduce(fdlbm_s* h, const void* state, int what, double a0, double a1,
+                          double* partial, double* result);
+
+}  // namespace fdlbm

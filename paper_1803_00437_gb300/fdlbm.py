@@ -1,0 +1,275 @@
+"""Python binding of the C-ABI library ``libfdlbm.so`` (include/fdlbm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels behind the C ABI.  PyTorch provides device memory (the workspace and
+field tensors) and CUDA streams.  There is no fallback: if the library is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdlbm.so")
+
+# include/fdlbm.h constants
+OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6)
+SCHEMES = {"fd3": 3, "fd5": 5, "mrt": 100}
+BOUNDARIES = {"periodic": 0, "walls_y": 1}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
+REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}
+
+
+class FdlbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("scheme", ctypes.c_int32), ("boundary", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("s_xx", ctypes.c_double), ("s_e", ctypes.c_double),
+        ("s_q", ctypes.c_double), ("s_eps", ctypes.c_double),
+        ("wall_xi", ctypes.c_double),
+        ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libfdlbm.so (built by paper_1803_00437_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise FdlbmError(ERR_CUDA, f"{p} is missing: build it with "
+                             "`python -m paper_1803_00437_gb300.build`")
+        L = ctypes.CDLL(p)
+        vp, cp = ctypes.c_void_p, ctypes.c_char_p
+        pp = ctypes.POINTER(Params)
+        fp = ctypes.c_void_p  # float* / double* passed as addresses
+        L.fdlbm_workspace_size.argtypes = [pp]
+        L.fdlbm_workspace_size.restype = ctypes.c_size_t
+        L.fdlbm_create.argtypes = [pp, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.fdlbm_destroy.argtypes = [vp]
+        L.fdlbm_destroy.restype = None
+        L.fdlbm_set_stream.argtypes = [vp, vp]
+        L.fdlbm_init.argtypes = [vp, fp, fp, fp]
+        L.fdlbm_init_host.argtypes = [vp, fp, fp, fp]
+        L.fdlbm_init_modes.argtypes = [vp, ctypes.c_int32, fp, ctypes.c_double, ctypes.c_double]
+        L.fdlbm_step.argtypes = [vp, ctypes.c_int64]
+        L.fdlbm_moments.argtypes = [vp, fp, fp, fp]
+        L.fdlbm_moments_host.argtypes = [vp, fp, fp, fp]
+        L.fdlbm_reduce.argtypes = [vp, ctypes.c_int32, fp, fp]
+        L.fdlbm_sync.argtypes = [vp]
+        L.fdlbm_last_error.argtypes = [vp]
+        L.fdlbm_last_error.restype = cp
+        L.fdlbm_status_string.argtypes = [ctypes.c_int]
+        L.fdlbm_status_string.restype = cp
+        L.fdlbm_launch_count.argtypes = [vp]
+        L.fdlbm_launch_count.restype = ctypes.c_int64
+        for name in ("fdlbm_create", "fdlbm_set_stream", "fdlbm_init", "fdlbm_init_host",
+                     "fdlbm_init_modes", "fdlbm_step", "fdlbm_moments", "fdlbm_moments_host",
+                     "fdlbm_reduce", "fdlbm_sync"):
+            getattr(L, name).restype = ctypes.c_int
+        if path is None:
+            _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    return load_library().fdlbm_status_string(int(status)).decode()
+
+
+def nu_to_s(nu: float) -> float:
+    """Sec. 1-a: nu = (1/s_xx - 1/2)/3, so s_xx = 1 / (3 nu + 1/2)."""
+    return 1.0 / (3.0 * nu + 0.5)
+
+
+def quartic_s_q(s_xx: float) -> float:
+    """Eq. sigsig: (1/s_xx - 1/2)(1/s_q - 1/2) = 1/6."""
+    return 1.0 / (1.0 / (6.0 * (1.0 / s_xx - 0.5)) + 0.5)
+
+
+@dataclass
+class LatticeConfig:
+    nx: int
+    ny: int
+    scheme: str = "fd5"
+    boundary: str = "periodic"
+    storage: str = "f32"
+    s_xx: float = 1.85
+    s_e: float = 1.5
+    s_q: float | None = None
+    s_eps: float = 1.5
+    wall_xi: float = 0.5
+    force: tuple = (0.0, 0.0)
+
+    def params(self) -> Params:
+        s_q = self.s_q if self.s_q is not None else (
+            quartic_s_q(self.s_xx) if self.scheme == "mrt" else 1.0)
+        return Params(int(self.nx), int(self.ny), SCHEMES[self.scheme],
+                      BOUNDARIES[self.boundary], STORAGES[self.storage], 0,
+                      float(self.s_xx), float(self.s_e), float(s_q), float(self.s_eps),
+                      float(self.wall_xi), float(self.force[0]), float(self.force[1]))
+
+
+def workspace_size(cfg: LatticeConfig) -> int:
+    p = cfg.params()
+    return int(load_library().fdlbm_workspace_size(ctypes.byref(p)))
+
+
+def _addr(t) -> int:
+    import torch
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    raise TypeError("expected a torch tensor")
+
+
+class Lattice:
+    """One D2Q9 lattice (FD-LBM or MRT) on one GPU.
+
+    The workspace is a torch uint8 tensor on the device (allocated here unless
+    given); every call is enqueued on `stream` (a torch.cuda.Stream; default:
+    the current stream of the device)."""
+
+    def __init__(self, cfg: LatticeConfig, device=None, stream=None, workspace=None):
+        import torch
+        self.cfg = cfg
+        self.lib = load_library()
+        self.params = cfg.params()
+        nbytes = int(self.lib.fdlbm_workspace_size(ctypes.byref(self.params)))
+        if nbytes == 0:
+            raise FdlbmError(ERR_INVALID, f"invalid lattice parameters {cfg}")
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise FdlbmError(ERR_NOMEM, "workspace too small")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.fdlbm_create(ctypes.byref(self.params), ctypes.c_void_p(_addr(workspace)),
+                                       nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(self._h))
+        if rc != OK:
+            raise FdlbmError(rc, f"fdlbm_create failed: {status_string(rc)}")
+        self.workspace_bytes = nbytes
+
+    # -- helpers --------------------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != OK:
+            msg = self.lib.fdlbm_last_error(self._h).decode()
+            raise FdlbmError(rc, f"{what}: {status_string(rc)}: {msg}")
+
+    def _field(self, t):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.is_cuda
+                and t.device == self.device and t.is_contiguous()
+                and t.numel() == self.cfg.nx * self.cfg.ny):
+            raise ValueError("fields must be contiguous float32 CUDA tensors of nx*ny elements "
+                             "on the lattice's device")
+        return ctypes.c_void_p(t.data_ptr())
+
+    @staticmethod
+    def _host(a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        return a, ctypes.c_void_p(a.ctypes.data)
+
+    # -- API ------------------------------------------------------------------------
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.fdlbm_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)),
+                    "set_stream")
+
+    def init(self, drho, ux, uy):
+        """drho, ux, uy: float32 CUDA tensors [ny, nx]."""
+        self._check(self.lib.fdlbm_init(self._h, self._field(drho), self._field(ux),
+                                        self._field(uy)), "init")
+
+    def init_host(self, drho, ux, uy):
+        """drho, ux, uy: host arrays [ny, nx] (converted to float32)."""
+        n = self.cfg.nx * self.cfg.ny
+        arrs = [self._host(np.asarray(a).reshape(-1)) for a in (drho, ux, uy)]
+        for a, _ in arrs:
+            if a.size != n:
+                raise ValueError("fields must have nx*ny elements")
+        self._check(self.lib.fdlbm_init_host(self._h, *[p for _, p in arrs]), "init_host")
+
+    def init_modes(self, modes, mean_velocity=(0.0, 0.0)):
+        """modes: iterable of (m, n, amplitude, phase) (e.g. inputs.Mode)."""
+        rec = np.ascontiguousarray(
+            [[float(md[0]), float(md[1]), float(md[2]), float(md[3])] if not hasattr(md, "m")
+             else [float(md.m), float(md.n), float(md.amp), float(md.phase)] for md in modes],
+            dtype=np.float64).reshape(-1)
+        ptr = ctypes.c_void_p(rec.ctypes.data) if rec.size else None
+        self._check(self.lib.fdlbm_init_modes(self._h, rec.size // 4, ptr,
+                                              float(mean_velocity[0]), float(mean_velocity[1])),
+                    "init_modes")
+
+    def step(self, nsteps: int = 1):
+        self._check(self.lib.fdlbm_step(self._h, int(nsteps)), "step")
+
+    def moments(self, out=None):
+        """(drho, ux, uy) as float32 CUDA tensors [ny, nx]."""
+        import torch
+        if out is None:
+            out = [torch.empty((self.cfg.ny, self.cfg.nx), dtype=torch.float32,
+                               device=self.device) for _ in range(3)]
+        self._check(self.lib.fdlbm_moments(self._h, *[self._field(t) for t in out]), "moments")
+        return tuple(out)
+
+    def moments_host(self):
+        out = [np.empty((self.cfg.ny, self.cfg.nx), dtype=np.float32) for _ in range(3)]
+        self._check(self.lib.fdlbm_moments_host(
+            self._h, *[ctypes.c_void_p(a.ctypes.data) for a in out]), "moments_host")
+        return tuple(out)
+
+    def reduce(self, what: str, args=None) -> np.ndarray:
+        out = np.zeros(4, dtype=np.float64)
+        a = None
+        if args is not None:
+            a = np.ascontiguousarray(args, dtype=np.float64)
+        rc = self.lib.fdlbm_reduce(self._h, REDUCE[what],
+                                   ctypes.c_void_p(a.ctypes.data) if a is not None else None,
+                                   ctypes.c_void_p(out.ctypes.data))
+        self._check(rc, f"reduce({what})")
+        n = 2 if what in ("momentum", "mode", "maxabs") else 1
+        return out[:n].copy()
+
+    def sync(self):
+        self._check(self.lib.fdlbm_sync(self._h), "sync")
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.fdlbm_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.fdlbm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerance (FP32 storage and arithmetic): max |gpu - oracle| over rho - 1,
+ux and uy, divided by the velocity amplitude of the initial field, at most
+1e-5 (the FP32 bound stated for the scheme after 1000 steps)."""
+import numpy as np
+import pytest
+
+from paper_1803_00437_gb300 import inputs
+from parity_util import amplitude, as_f32, gpu_run, max_err, oracle_run
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_00437_gb300 import build
+    build.build()
+
+
+def _cfg(nx, ny, scheme, **kw):
+    from paper_1803_00437_gb300 import fdlbm as F
+    return F.LatticeConfig(nx, ny, scheme, **kw)
+
+
+def _nu(nu):
+    return 1.0 / (3.0 * nu + 0.5)
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+def test_shear_wave_64_1000_steps(oracle, scheme):
+    """64x64 periodic shear wave ux = 0.01 sin(2 pi y/64), nu = 0.01, 1000 steps."""
+    f = as_f32(inputs.shear_wave(64, 64, 0.01, m=0, n=1, phase=np.pi / 2))
+    cfg = _cfg(64, 64, scheme, s_xx=_nu(0.01), s_e=1.5)
+    gpu, _ = gpu_run(cfg, f, 1000)
+    ref = oracle_run(oracle, cfg, f, 1000)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+def test_random_modes_ragged_tiles(oracle, scheme):
+    """200 x 136 periodic (several tiles plus a ragged tail in x and y),
+    32 seeded transverse modes of amplitude 1e-3, 300 steps."""
+    modes = inputs.random_modes(200, 136, 32, 1e-3, seed=inputs.seed_for(1))
+    f = as_f32(inputs.transverse_modes(200, 136, modes))
+    cfg = _cfg(200, 136, scheme, s_xx=_nu(0.01), s_e=1.5)
+    gpu, _ = gpu_run(cfg, f, 300)
+    ref = oracle_run(oracle, cfg, f, 300)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+@pytest.mark.parametrize("shape", [(37, 29), (5, 3), (16, 1), (1, 16), (33, 17)])
+def test_nonlinear_small_and_degenerate(oracle, scheme, shape):
+    """Seeded noise of amplitude 0.02 with density noise (nonlinear terms
+    active), lattices smaller than a tile and thinner than the halo."""
+    nx, ny = shape
+    f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=nx * 100 + ny, rho_amp=0.005))
+    cfg = _cfg(nx, ny, scheme, s_xx=1.6, s_e=1.4)
+    gpu, _ = gpu_run(cfg, f, 40)
+    ref = oracle_run(oracle, cfg, f, 40)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme,xi", [("fd3", 0.5), ("fd5", 0.5), ("fd5", 0.3), ("fd3", 1.0),
+                                       ("fd5", 0.8), ("mrt", 0.5)])
+def test_channel_walls_with_force(oracle, scheme, xi):
+    """Channel 40 x 24 (periodic in x, walls in y) with a body force and a
+    seeded non-uniform start, 300 steps."""
+    f = inputs.random_fields(40, 24, 0.01, seed=77, rho_amp=0.002)
+    f = as_f32(f)
+    cfg = _cfg(40, 24, scheme, s_xx=_nu(1 / np.sqrt(108)), s_e=1.5, boundary="walls_y",
+               wall_xi=xi, force=(2e-5, -1e-6))
+    gpu, _ = gpu_run(cfg, f, 300)
+    ref = oracle_run(oracle, cfg, f, 300)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme", ["fd5", "mrt"])
+def test_poiseuille_channel_256x64(oracle, scheme):
+    """Poiseuille channel 256 x 64, walls at xi = 1/2, force for u_max = 0.05,
+    nu = 1/sqrt(108), 3000 steps from rest.  The flow is x-invariant, so the
+    oracle runs 4 columns of the same channel.
+
+    Tolerance: with FP32 storage the per-step force increment F ~ 1e-5 is
+    added to u ~ 0.025 whose spacing is 1.9e-9, so each increment carries a
+    relative rounding of ~2e-4 that repeats at a node while the flow is
+    quasi-steady; the accumulated error is bounded by eps * min(n, T) with
+    T = H^2 / (pi^2 nu) the viscous time (4300 steps), eps = 6e-8: 2e-4 of
+    u_max."""
+    nu = 1 / np.sqrt(108)
+    H = 64
+    F = 8 * nu * 0.05 / H ** 2
+    cfg = _cfg(256, 64, scheme, s_xx=_nu(nu), s_e=1.5, boundary="walls_y", wall_xi=0.5,
+               force=(F, 0.0))
+    f = as_f32(inputs.channel_at_rest(256, 64))
+    gpu, _ = gpu_run(cfg, f, 3000)
+    cfg4 = _cfg(4, 64, scheme, s_xx=_nu(nu), s_e=1.5, boundary="walls_y", wall_xi=0.5,
+                force=(F, 0.0))
+    ref = oracle_run(oracle, cfg4, as_f32(inputs.channel_at_rest(4, 64)), 3000)
+    umax = float(np.abs(ref[1]).max())
+    tol = 6e-8 * min(3000, H * H / (np.pi ** 2 * nu))
+    for g, r in zip(gpu, ref):
+        assert np.abs(g - r[:, :1]).max() <= tol * umax
+
+
+def test_zero_steps_returns_initial_state(oracle):
+    f = as_f32(inputs.random_fields(24, 20, 0.02, seed=1, rho_amp=0.01))
+    for scheme in ("fd3", "fd5"):
+        gpu, _ = gpu_run(_cfg(24, 20, scheme), f, 0)
+        for g, r in zip(gpu, f):
+            assert np.array_equal(g.astype(np.float32), r)
+    gpu, _ = gpu_run(_cfg(24, 20, "mrt"), f, 0)
+    assert max_err(gpu, [x.astype(np.float64) for x in f], amplitude(f)) < 1e-6
+
+
+_FULL = {}
+
+
+def _full_size_fields(N):
+    if N not in _FULL:
+        modes = inputs.random_modes(N, N, 32, 1e-3, seed=inputs.seed_for(1))
+        _FULL[N] = as_f32(inputs.transverse_modes(N, N, modes))
+    return _FULL[N]
+
+
+@pytest.mark.parametrize("scheme", ["fd5", "mrt"])
+def test_full_size_sampled_8192(oracle, scheme):
+    """8192 x 8192 periodic, 32 seeded modes of amplitude 1e-3 (the throughput
+    lattice), one step in the benchmark's launch configuration, compared at
+    4096 sampled nodes (including the four edges) against the oracle's
+    point-wise step."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    N = 8192
+    f = _full_size_fields(N)
+    cfg = F.LatticeConfig(N, N, scheme, s_xx=_nu(0.01), s_e=1.5)
+    lat = F.Lattice(cfg)
+    dev = [torch.from_numpy(a).to(lat.device) for a in f]
+    lat.init(*dev)
+    lat.step(1)
+    out = [t.cpu().numpy() for t in lat.moments()]
+    lat.close()
+    del dev, lat
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, N * N, 4000)
+    edges = np.array([0, N - 1, N * (N - 1), N * N - 1] +
+                     list(rng.integers(0, N, 24)) + list(rng.integers(0, N, 24) * N) +
+                     list(rng.integers(0, N, 24) * N + N - 1) + list(N * (N - 1) + rng.integers(0, N, 24)))
+    idx = np.concatenate([idx, edges]).astype(np.int64)
+    from parity_util import oracle_params
+    p = oracle_params(oracle, cfg)
+    d, x, y = (a.astype(np.float64) for a in f)
+    if scheme == "mrt":
+        ref = oracle.mrt_step_points_from_eq(p, 1.0 + d, x, y, idx)
+    else:
+        ref = oracle.fd_step_points(p, 1.0 + d, x, y, idx)
+    A = amplitude(f)
+    assert np.abs(out[0].ravel()[idx] - (ref[:, 0] - 1.0)).max() <= TOL32 * A
+    assert np.abs(out[1].ravel()[idx] - ref[:, 1]).max() <= TOL32 * A
+    assert np.abs(out[2].ravel()[idx] - ref[:, 2]).max() <= TOL32 * A
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+def test_fp64_reductions_and_conservation(oracle, scheme):
+    """FP64 reductions on the device match numpy on the moments; mass and
+    momentum are conserved on a periodic lattice over 1000 steps."""
+    from paper_1803_00437_gb300 import fdlbm as F
+    import torch
+    modes = inputs.random_modes(96, 80, 8, 2e-3, seed=3)
+    f = as_f32(inputs.transverse_modes(96, 80, modes))
+    f = (as_f32(inputs.random_fields(96, 80, 0.0, seed=4, rho_amp=1e-3))[0], f[1], f[2])
+    cfg = _cfg(96, 80, scheme, s_xx=_nu(0.02), s_e=1.5)
+    lat = F.Lattice(cfg)
+    lat.init(*[torch.from_numpy(a).to(lat.device) for a in f])
+    m0, p0 = lat.reduce("mass")[0], lat.reduce("momentum")
+    lat.step(1000)
+    d, ux, uy = (t.cpu().numpy().astype(np.float64) for t in lat.moments())
+    m1, p1 = lat.reduce("mass")[0], lat.reduce("momentum")
+    assert abs(m1 - d.sum()) < 1e-9 and abs(m1 - m0) < 1e-6
+    rho = 1 + d
+    assert np.abs(p1 - [(rho * ux).sum(), (rho * uy).sum()]).max() < 1e-9
+    assert np.abs(p1 - p0).max() < 1e-5
+    e = lat.reduce("energy")[0]
+    assert abs(e - 0.5 * (rho * (ux ** 2 + uy ** 2)).sum()) < 1e-9 * max(1.0, e)
+    mx = lat.reduce("maxabs")
+    assert abs(mx[0] - np.sqrt(ux ** 2 + uy ** 2).max()) < 1e-9
+    md = modes[0]
+    c = lat.reduce("mode", (md.m, md.n))
+    X, Y = np.meshgrid(np.arange(96), np.arange(80))
+    kx, ky = 2 * np.pi * md.m / 96, 2 * np.pi * md.n / 80
+    k = np.hypot(kx, ky)
+    ut = (-ky * ux + kx * uy) / k
+    ref = (ut * np.exp(-1j * (kx * X + ky * Y))).mean()
+    assert abs(c[0] - ref.real) < 1e-10 and abs(c[1] - ref.imag) < 1e-10
+
+
+def test_init_modes_matches_inputs():
+    """The device-side initial field equals the seeded generator's."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    modes = inputs.random_modes(300, 200, 32, 1e-3, seed=9)
+    ref = inputs.transverse_modes(300, 200, modes, (0.01, -0.02))
+    lat = F.Lattice(_cfg(300, 200, "fd5"))
+    lat.init_modes(modes, (0.01, -0.02))
+    out = [t.cpu().numpy() for t in lat.moments()]
+    for o, r in zip(out, ref):
+        assert np.abs(o - r).max() < 1e-9
+
+
+def test_host_round_trip_and_errors():
+    from paper_1803_00437_gb300 import fdlbm as F
+    f = as_f32(inputs.random_fields(50, 30, 0.02, seed=2, rho_amp=0.01))
+    lat = F.Lattice(_cfg(50, 30, "fd5"))
+    lat.init_host(*f)
+    out = lat.moments_host()
+    for o, r in zip(out, f):
+        assert np.array_equal(o, r)
+    with pytest.raises(F.FdlbmError):
+        lat.step(-1)
+    with pytest.raises(F.FdlbmError):
+        F.Lattice(_cfg(50, 30, "mrt", storage="bf16"))
+    bad = np.full((30, 50), np.nan, dtype=np.float32)
+    lat.init_host(bad, f[1], f[2])
+    with pytest.raises(F.FdlbmError) as ei:
+        lat.reduce("mass")
+    assert ei.value.status == F.ERR_DIVERGED
+    assert lat.launches > 0
