@@ -32,9 +32,9 @@
  *     the small host-side handle; it never calls cudaMalloc or cudaFree.
  *   - Errors: every int-returning call returns FDLBM_OK (0) or a negative
  *     fdlbm_status.  Nothing aborts or throws.  The text of the last error on
- *     a handle is available from fdlbm_last_error.  Errors found on the
- *     device (a non-finite velocity, see fdlbm_check) are reported by the
- *     next call that waits for the stream.
+ *     a handle is available from fdlbm_last_error.  A device-side wait that
+ *     ran out (FDLBM_ERR_TIMEOUT) is reported by the next fdlbm_sync or
+ *     fdlbm_reduce; non-finite values by fdlbm_reduce (FDLBM_ERR_DIVERGED).
  *   - A handle may be used by one host thread at a time.
  */
 #ifndef FDLBM_H
@@ -69,6 +69,12 @@ extern "C" {
 #define FDLBM_STORAGE_F16 1  /* FD-LBM only: (rho-1, ux, uy) in FP16, FP32 math */
 #define FDLBM_STORAGE_BF16 2 /* FD-LBM only: (rho-1, ux, uy) in BF16, FP32 math */
 
+/* FD-LBM kernels: periodic lattices with nx % 8 == 0, nx >= 256, ny >= 16 use
+ * the streaming kernel (TMA-staged rows, register window); every other case
+ * uses the general tiled kernel.  FDLBM_FLAG_TILED forces the tiled kernel
+ * (same results up to FP32 rounding; used to cross-check the two). */
+#define FDLBM_FLAG_TILED 1
+
 /* Parameters of one lattice.  Relaxation rates lie in (0, 2).
  *   s_xx : rate of XX and XY; shear viscosity nu = (1/s_xx - 1/2)/3 (Sec. 1-a)
  *   s_e  : rate of E; bulk viscosity zeta = (1/s_e - 1/2)/3 (Sec. 1-a)
@@ -82,7 +88,7 @@ typedef struct fdlbm_params {
     int32_t scheme;   /* FDLBM_SCHEME_*   */
     int32_t boundary; /* FDLBM_BOUNDARY_* */
     int32_t storage;  /* FDLBM_STORAGE_*  */
-    int32_t flags;    /* reserved, must be 0 */
+    int32_t flags;    /* 0, or FDLBM_FLAG_* bits */
     double s_xx, s_e, s_q, s_eps;
     double wall_xi;
     double force_x, force_y;

@@ -30,7 +30,7 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->storage != FDLBM_STORAGE_F32 && p->storage != FDLBM_STORAGE_F16 &&
         p->storage != FDLBM_STORAGE_BF16)
         return fail(FDLBM_ERR_INVALID, "storage must be F32, F16 or BF16");
-    if (p->flags != 0) return fail(FDLBM_ERR_INVALID, "flags must be 0");
+    if ((p->flags & ~FDLBM_FLAG_TILED) != 0) return fail(FDLBM_ERR_INVALID, "unknown flags");
     if (!valid_rate(p->s_xx) || !valid_rate(p->s_e))
         return fail(FDLBM_ERR_INVALID, "s_xx and s_e must lie in (0, 2)");
     if (p->scheme == FDLBM_SCHEME_MRT && (!valid_rate(p->s_q) || !valid_rate(p->s_eps)))
@@ -108,6 +108,21 @@ struct DeviceGuard {
     }
 };
 
+// Read (and clear) the device status word after the stream has drained.
+static int device_status(fdlbm_t* h) {
+    int flag = 0;
+    int* dflag = reinterpret_cast<int*>(h->ws + h->L.off_flag);
+    cudaError_t e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (flag != 0) {
+        cudaMemsetAsync(dflag, 0, sizeof(int), h->stream);
+        return set_error(h, flag, "device reported %s (a bounded wait expired)",
+                         flag == FDLBM_ERR_TIMEOUT ? "FDLBM_ERR_TIMEOUT" : "an error");
+    }
+    return FDLBM_OK;
+}
+
 extern "C" {
 
 size_t fdlbm_workspace_size(const fdlbm_params* p) {
@@ -137,6 +152,8 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
     h->ws = static_cast<char*>(workspace);
     h->cur = 0;
     h->launches = 0;
+    h->stream_plan_warps = 0;
+    h->fd_path = (p->flags & FDLBM_FLAG_TILED) ? 1 : 0;
     h->err[0] = 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
@@ -148,6 +165,11 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
         cudaGetLastError();
         delete h;
         return FDLBM_ERR_INVALID;
+    }
+    if (cudaMemsetAsync(h->ws + h->L.off_flag, 0, sizeof(int), h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return FDLBM_ERR_CUDA;
     }
     *out = h;
     return FDLBM_OK;
@@ -297,7 +319,7 @@ int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out) {
     if (host[3] != 0.0)
         return set_error(h, FDLBM_ERR_DIVERGED, "reduce: %.0f nodes hold non-finite values",
                          host[3]);
-    return FDLBM_OK;
+    return device_status(h);
 }
 
 int fdlbm_sync(fdlbm_t* h) {
@@ -305,7 +327,7 @@ int fdlbm_sync(fdlbm_t* h) {
     DeviceGuard g(h->device);
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sync");
-    return FDLBM_OK;
+    return device_status(h);
 }
 
 const char* fdlbm_last_error(const fdlbm_t* h) { return h ? h->err : "NULL handle"; }
@@ -329,6 +351,7 @@ int64_t fdlbm_launch_count(const fdlbm_t* h) { return h ? h->launches : -1; }
 
 namespace fdlbm {
 cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
+    if (h->fd_path == 0 && fd_stream_supported(h->p)) return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }
 }  // namespace fdlbm

@@ -101,6 +101,8 @@ struct fdlbm_s {
     char* ws;
     int cur;  // index of the current state copy
     int64_t launches;
+    int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
+    int fd_path;            // 0: automatic, 1: force the tiled FD kernel
     char err[512];
 };
 
@@ -111,6 +113,8 @@ MrtCoeffs mrt_coeffs(const fdlbm_params& p);
 // launchers (each returns cudaGetLastError() of its launch)
 cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst);
+cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst);
+bool fd_stream_supported(const fdlbm_params& p);
 cudaError_t launch_mrt_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
                            void* dst);

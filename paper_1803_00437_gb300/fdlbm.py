@@ -24,6 +24,7 @@ SCHEMES = {"fd3": 3, "fd5": 5, "mrt": 100}
 BOUNDARIES = {"periodic": 0, "walls_y": 1}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}
+FLAG_TILED = 1
 
 
 class FdlbmError(RuntimeError):
@@ -118,12 +119,13 @@ class LatticeConfig:
     s_eps: float = 1.5
     wall_xi: float = 0.5
     force: tuple = (0.0, 0.0)
+    flags: int = 0
 
     def params(self) -> Params:
         s_q = self.s_q if self.s_q is not None else (
             quartic_s_q(self.s_xx) if self.scheme == "mrt" else 1.0)
         return Params(int(self.nx), int(self.ny), SCHEMES[self.scheme],
-                      BOUNDARIES[self.boundary], STORAGES[self.storage], 0,
+                      BOUNDARIES[self.boundary], STORAGES[self.storage], int(self.flags),
                       float(self.s_xx), float(self.s_e), float(s_q), float(self.s_eps),
                       float(self.wall_xi), float(self.force[0]), float(self.force[1]))
 

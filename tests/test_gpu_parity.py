@@ -232,3 +232,34 @@ def test_host_round_trip_and_errors():
         lat.reduce("mass")
     assert ei.value.status == F.ERR_DIVERGED
     assert lat.launches > 0
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5"])
+@pytest.mark.parametrize("shape", [(256, 64), (264, 40), (512, 37), (384, 100), (1024, 16)])
+def test_streaming_kernel_parity(oracle, scheme, shape):
+    """Periodic lattices taking the streaming FD-LBM kernel: several warp
+    strips, a partial last strip (264 = 2 x 120 + 24), odd row counts and
+    several row segments; 32 seeded modes plus density noise, 200 steps."""
+    nx, ny = shape
+    modes = inputs.random_modes(nx, ny, 32, 2e-3, seed=nx + ny)
+    d, ux, uy = inputs.transverse_modes(nx, ny, modes)
+    d = inputs.random_fields(nx, ny, 0.0, seed=3, rho_amp=1e-3)[0]
+    f = as_f32((d, ux, uy))
+    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.01), s_e=1.5)
+    gpu, _ = gpu_run(cfg, f, 200)
+    ref = oracle_run(oracle, cfg, f, 200)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme", ["fd3", "fd5"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_streaming_equals_tiled(scheme, storage):
+    """Both FD-LBM kernels give the same lattice (FP32 arithmetic in both;
+    they differ only in the order of roundings)."""
+    nx, ny = 392, 72
+    f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=8, rho_amp=0.005))
+    from paper_1803_00437_gb300 import fdlbm as F
+    a, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage), f, 30)
+    b, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage, flags=F.FLAG_TILED), f, 30)
+    tol = {"f32": 1e-5, "f16": 2e-2, "bf16": 1e-1}[storage]
+    assert max_err(a, b, amplitude(f)) <= tol
