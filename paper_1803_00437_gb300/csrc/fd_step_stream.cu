@@ -9,16 +9,18 @@
 // other.
 //
 // Data path per warp.  Rows of (rho - 1, ux, uy) for the strip plus 8 halo
-// columns are copied by 1-D bulk (TMA) copies into a private ring of
-// shared-memory slots, each slot completed by an mbarrier, several rows
-// ahead of use.  Each lane reads its 4 columns (one 16-byte load per field
-// for FP32).  Derivatives along y use a register window over rows (for five
-// points, d1(c) = f(c+1) - f(c-1) and 8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1),
-// so four rows are held); derivatives along x use warp shuffles of the two
-// neighbouring columns on each side.  After the reconstruction the
+// columns are copied by 1-D bulk (TMA) copies into a private ring of 8
+// shared-memory slots, each completed by an mbarrier, several rows ahead of
+// use (two rows per issue, six lanes issuing one copy each).  Each lane
+// reads its 4 columns (one 16-byte load per field for FP32).  Derivatives
+// along y: three points hold the two previous rows in registers; five points
+// hold only the (negated) differences d1(c) = f(c+1) - f(c-1) and use
+// 8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), the centre row being re-read from the
+// ring.  Derivatives along x use warp shuffles of the two neighbouring
+// columns on each side.  Arithmetic on column pairs uses the paired FP32
+// instructions of sm_100-family GPUs.  After the reconstruction the
 // populations that cross a lane boundary are exchanged by shuffles, summed
 // per destination row and closed when the row below has contributed.
-// Outputs are written with 16-byte (FP32) stores.
 #include <algorithm>
 
 #include "fd_common.cuh"
@@ -30,24 +32,35 @@ namespace {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kStrip = 120;     // output columns per warp
 constexpr int kLoadCols = 136;  // columns staged per row: strip0 - 8 .. strip0 + 128
-constexpr int kSlots = 6;       // ring depth (rows)
-// Resident CTAs per SM requested from the register allocator (168
-// registers for three): measured on GB300, three is fastest for both
-// stencils (five points: 137.5 vs 133.8 GLUPS at two).
+constexpr int kSlots = 8;       // ring depth (rows); a power of two
+constexpr int kSlotMask = kSlots - 1;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Resident CTAs per SM requested from the register allocator (168 registers
+// for three); measured on GB300, three is fastest for both stencils.
 #ifndef FDLBM_STREAM_MIN_BLOCKS5
 #define FDLBM_STREAM_MIN_BLOCKS5 3
 #endif
 template <int R>
-constexpr int min_blocks() { return R == 1 ? 3 : FDLBM_STREAM_MIN_BLOCKS5; }
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int min_blocks() {
+    return R == 1 ? 3 : FDLBM_STREAM_MIN_BLOCKS5;
+}
 
-// Paired FP32 arithmetic (two lattice columns per instruction).
+// ---- paired FP32 arithmetic (two lattice columns per instruction) --------------
+
 __device__ __forceinline__ float2 sp(float c) { return make_float2(c, c); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-// a - b (b * -1 is exact, so this rounds once like a subtraction)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, sp(-1.f), a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 
 // Hardware reciprocal (relative error ~2^-23).  Used only where it scales a
 // small correction term, so its error is far below FP32 resolution.
@@ -57,28 +70,30 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// ---- storage of 4 consecutive columns ----------------------------------------------
+
 template <typename T>
 struct Vec4;
 template <>
 struct Vec4<float> {
-    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+    static __device__ __forceinline__ void load(const float* p, float2 v[2]) {
         const float4 q = *reinterpret_cast<const float4*>(p);
-        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
     }
-    static __device__ __forceinline__ void store(float* p, const float v[4]) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    static __device__ __forceinline__ void store(float* p, const float2 v[2]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
     }
 };
 template <>
 struct Vec4<__half> {
-    static __device__ __forceinline__ void load(const __half* p, float v[4]) {
+    static __device__ __forceinline__ void load(const __half* p, float2 v[2]) {
         const uint2 q = *reinterpret_cast<const uint2*>(p);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        v[0] = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        v[1] = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
     }
-    static __device__ __forceinline__ void store(__half* p, const float v[4]) {
-        __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    static __device__ __forceinline__ void store(__half* p, const float2 v[2]) {
+        __half2 a = __float22half2_rn(v[0]), b = __float22half2_rn(v[1]);
         uint2 q;
         q.x = *reinterpret_cast<uint32_t*>(&a);
         q.y = *reinterpret_cast<uint32_t*>(&b);
@@ -87,15 +102,13 @@ struct Vec4<__half> {
 };
 template <>
 struct Vec4<__nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16* p, float v[4]) {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, float2 v[2]) {
         const uint2 q = *reinterpret_cast<const uint2*>(p);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        v[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        v[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
     }
-    static __device__ __forceinline__ void store(__nv_bfloat16* p, const float v[4]) {
-        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
-        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, const float2 v[2]) {
+        __nv_bfloat162 a = __float22bfloat162_rn(v[0]), b = __float22bfloat162_rn(v[1]);
         uint2 q;
         q.x = *reinterpret_cast<uint32_t*>(&a);
         q.y = *reinterpret_cast<uint32_t*>(&b);
@@ -103,75 +116,82 @@ struct Vec4<__nv_bfloat16> {
     }
 };
 
-// Fields kept in the y window: rho - 1, Jx, Jy, Jx Jy / rho, Jy Jy / rho.
+// Fields of the y window: rho - 1, Jx, Jy, Jx Jy / rho, Jy Jy / rho, each as
+// two column pairs: v[f][0] = columns (0, 1), v[f][1] = columns (2, 3).
 enum { W_R = 0, W_JX, W_JY, W_PXY, W_PYY, W_N };
 
-// v[f][0] holds columns (0, 1), v[f][1] columns (2, 3) of this lane.
 struct Win {
     float2 v[W_N][2];
 };
 
+// Relaxation factors with the derivative scale (2 or 8) and the constants
+// of theta and of M^-1 folded in (see reconstruct2).
+struct StreamCoeffs {
+    float e6, e2, em2;         // theta_E terms, times (1 - 1/s_e) / (36 scale)
+    float x23, xm2, x13, xm1;  // theta_XX, theta_XY terms, times (1 - 1/s_xx) / scale
+    float hfx, hfy;            // half of the body force
+};
+
 struct StreamArgs {
-    const void* src;   // 3 planes (rho - 1, ux, uy), [ny][pitch]
+    const void* src;  // 3 planes (rho - 1, ux, uy), [ny][pitch]
     void* dst;
-    size_t plane;      // elements per plane
-    size_t pitch;      // elements per row
+    size_t plane;     // elements per plane
+    size_t pitch;     // elements per row
     int nx, ny;
     int nstrips, seg_rows, nsegs, nitems;
-    FdCoeffs c;
-    int* status;       // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
+    StreamCoeffs k;
+    int* status;      // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
 };
 
 template <typename T>
 struct Ring {
-    T* slot_base;       // kSlots x 3 x kLoadCols elements
-    uint64_t* bars;     // kSlots barriers
+    T* slot_base;    // kSlots x 3 x kLoadCols elements
+    uint64_t* bars;  // kSlots barriers
 };
 
 template <typename T>
 __device__ __forceinline__ T* slot_field(const Ring<T>& ring, int slot, int field) {
-    return ring.slot_base + ((size_t)slot * 3 + field) * kLoadCols;
+    return ring.slot_base + (slot * 3 + field) * kLoadCols;
 }
 
-// Column pieces of a strip's staged row: kLoadCols columns starting at x0
-// (wrapping once at nx).  Fixed for a work item.
-struct Cols {
-    int x0, first;
+// Per-item constants of a warp.
+struct Item {
+    int strip0, yb, ye, row_first, nrows;
+    int x0, first;     // staged columns: kLoadCols from x0, wrapping once at nx
+    bool lane_stores;  // this lane's 4 columns are output columns
+    uint32_t base;     // ring position of the item's row 0
 };
 
-__device__ __forceinline__ Cols strip_cols(const StreamArgs& a, int strip0) {
-    Cols c;
-    c.x0 = wrap_index(strip0 - 8, a.nx);
-    c.first = min(kLoadCols, a.nx - c.x0);
-    return c;
-}
-
-// Issue the copies of one row (3 fields) into a slot; row already in
-// [0, ny).  Called by the whole warp: lane 0 arms the barrier with the
-// row's byte count, then lanes 0..2 each copy one field (one or two pieces).
+// Issue rows k0 .. k0 + count - 1 (count 1 or 2) of the item into their ring
+// slots: lanes 0..count-1 first arm the rows' barriers with the byte count,
+// then lanes 0..3 count - 1 each copy one field of one row.
 template <typename T>
-__device__ __forceinline__ void issue_row(const StreamArgs& a, const Ring<T>& ring, int slot,
-                                          int r, const Cols& cols, int lane) {
-    uint64_t* bar = &ring.bars[slot];
-    if (lane == 0) {
+__device__ __forceinline__ void issue_rows(const StreamArgs& a, const Ring<T>& ring,
+                                           const Item& it, int k0, int count, int lane) {
+    if (lane < count) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, 3u * kLoadCols * sizeof(T));
+        mbar_arrive_expect_tx(&ring.bars[(it.base + k0 + lane) & kSlotMask],
+                              3u * kLoadCols * sizeof(T));
     }
     __syncwarp();
-    if (lane < 3) {
+    if (lane < 3 * count) {
+        const int j = lane >= 3 ? 1 : 0;  // which row this lane copies
+        const int f = lane - 3 * j;       // which field
+        const int slot = (it.base + k0 + j) & kSlotMask;
+        int r = it.row_first + k0 + j;
+        if (r < 0) r += a.ny;
+        if (r >= a.ny) r -= a.ny;
         fence_proxy_async_smem();
-        const T* rowp = static_cast<const T*>(a.src) + lane * a.plane + (size_t)r * a.pitch;
-        T* dst = slot_field(ring, slot, lane);
-        tma_load_1d(dst, rowp + cols.x0, cols.first * sizeof(T), bar);
-        if (cols.first < kLoadCols)
-            tma_load_1d(dst + cols.first, rowp, (kLoadCols - cols.first) * sizeof(T), bar);
+        const T* rowp = static_cast<const T*>(a.src) + f * a.plane + (size_t)r * a.pitch;
+        T* dst = slot_field(ring, slot, f);
+        uint64_t* bar = &ring.bars[slot];
+        tma_load_1d(dst, rowp + it.x0, it.first * sizeof(T), bar);
+        if (it.first < kLoadCols)
+            tma_load_1d(dst + it.first, rowp, (kLoadCols - it.first) * sizeof(T), bar);
     }
 }
 
-__device__ __forceinline__ int next_row(int r, int ny) { return r + 1 == ny ? 0 : r + 1; }
-
-// x-derivative (scaled by 2 or 8) at the 4 columns of this lane of one
-// field given as two column pairs.
+// x-derivative (scaled by 2 or 8) at the 4 columns of this lane.
 template <int R>
 __device__ __forceinline__ void deriv_x(const float2 v[2], float2 d[2]) {
     const float f0 = v[0].x, f1 = v[0].y, f2 = v[1].x, f3 = v[1].y;
@@ -190,18 +210,54 @@ __device__ __forceinline__ void deriv_x(const float2 v[2], float2 d[2]) {
     }
 }
 
-// g = M^-1 m' in deviation form for two columns at once; same arithmetic
-// as moments_to_populations (conserved moments reproduced with unbiased
-// roundings: sx = (jx - 2 tx)/4, g0 = dr - 4 (axis + diag)), with q = -J.
-__device__ __forceinline__ void populations2(float2 dr, float2 jx, float2 jy, float2 Jx, float2 Jy,
-                                             float2 e, float2 xx, float2 xy, float2 ep,
-                                             float2 g[9]) {
-    const float2 r9 = mul2(dr, sp(1.f / 9.f));
-    const float2 axis = fma2(e, sp(-1.f / 36.f), fma2(ep, sp(-1.f / 18.f), r9));
-    const float2 diag = fma2(e, sp(1.f / 18.f), fma2(ep, sp(1.f / 36.f), r9));
+// Reconstruction (Sec. 2) of two columns, g_a = f*_a - w_a, from scaled
+// derivatives.  With K_E = (1 - 1/s_e) theta_E, K_XX, K_XY likewise and
+// u2 = |u|^2, the moments of the table of Sec. 2 substituted into M^-1 give
+//   g0 = dr - 4 (axis + diag)            (so that sum g = dr, unbiased)
+//   axis = dr/9 + rho u2/12 - K_E/36,     diag = dr/36 + rho u2/12 + K_E/18
+//   tx = (jx + Jx)/6, sx = (jx - 2 tx)/4 (so that sum c g = jx, unbiased)
+//   g1,3 = axis + XX/4 +- tx,  g2,4 = axis - XX/4 +- ty,
+//   g5,7 = diag + XY/4 +- (sx + sy),  g6,8 = diag - XY/4 +- (sy - sx),
+// with jx = Jx + F/2 (Strang) and q = -J, epsilon at equilibrium.
+template <bool FORCE>
+__device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, float2 Jx, float2 Jy,
+                                             float2 dxr, float2 dyr, float2 dxjx, float2 dyjx,
+                                             float2 dxjy, float2 dyjy, float2 dxpxx,
+                                             float2 dxpxy, float2 dypxy, float2 dypyy,
+                                             const StreamCoeffs& k, float2 g[9]) {
+    const float2 nuy = mul2(uy, sp(-1.f));
+    const float2 uxx = mul2(ux, ux), uyy = mul2(uy, uy), uxy = mul2(ux, uy);
+    const float2 u2 = add2(uxx, uyy);
+    const float2 mx = add2(dxpxx, dypxy);
+    const float2 my = add2(dxpxy, dypyy);
+    // K_E / 36 = a_e [(2 + 6 u^2)(d.J) - 2 (u . grad rho)] / 36
+    const float2 udr = fma2(uy, dyr, mul2(ux, dxr));
+    const float2 ke36 =
+        fma2(sp(k.em2), udr, mul2(fma2(sp(k.e6), u2, sp(k.e2)), add2(dxjx, dyjy)));
+    // K_XX = a_xx [2/3 ((dxJx - dyJy) - (ux dxr - uy dyr)) - 2 (ux mx - uy my)]
+    const float2 b = sub2(sub2(dxjx, dyjy), fma2(ux, dxr, mul2(nuy, dyr)));
+    const float2 kxx = fma2(sp(k.x23), b, mul2(sp(k.xm2), fma2(ux, mx, mul2(nuy, my))));
+    // K_XY = a_xx [1/3 ((dxJy + dyJx) - (ux dyr + uy dxr)) - (ux my + uy mx)]
+    const float2 c = sub2(add2(dxjy, dyjx), fma2(ux, dyr, mul2(uy, dxr)));
+    const float2 kxy = fma2(sp(k.x13), c, mul2(sp(k.xm1), fma2(ux, my, mul2(uy, mx))));
+    // equilibrium parts: rho u2, rho (ux^2 - uy^2), rho ux uy
+    const float2 ru2_12 = mul2(fma2(dr, u2, u2), sp(1.f / 12.f));
+    const float2 dxx = sub2(uxx, uyy);
+    const float2 xx = add2(fma2(dr, dxx, dxx), kxx);
+    const float2 xy = add2(fma2(dr, uxy, uxy), kxy);
+    const float2 axis = sub2(fma2(dr, sp(1.f / 9.f), ru2_12), ke36);
+    const float2 diag = fma2(sp(2.f), ke36, fma2(dr, sp(1.f / 36.f), ru2_12));
     g[0] = fma2(sp(-4.f), add2(axis, diag), dr);
-    const float2 tx = mul2(add2(jx, Jx), sp(1.f / 6.f));  // (jx - qx) / 6
-    const float2 ty = mul2(add2(jy, Jy), sp(1.f / 6.f));
+    float2 tx, ty, jx = Jx, jy = Jy;
+    if (FORCE) {
+        jx = add2(Jx, sp(k.hfx));
+        jy = add2(Jy, sp(k.hfy));
+        tx = mul2(add2(jx, Jx), sp(1.f / 6.f));
+        ty = mul2(add2(jy, Jy), sp(1.f / 6.f));
+    } else {
+        tx = mul2(Jx, sp(1.f / 3.f));
+        ty = mul2(Jy, sp(1.f / 3.f));
+    }
     const float2 sx = mul2(fma2(sp(-2.f), tx, jx), sp(0.25f));
     const float2 sy = mul2(fma2(sp(-2.f), ty, jy), sp(0.25f));
     const float2 ax = fma2(xx, sp(0.25f), axis), ay = fma2(xx, sp(-0.25f), axis);
@@ -217,37 +273,6 @@ __device__ __forceinline__ void populations2(float2 dr, float2 jx, float2 jy, fl
     g[8] = sub2(dm, smm);
 }
 
-// Reconstruction (Sec. 2) of two columns from scaled derivatives; the
-// derivative scale is folded into the relaxation factors a_e, a_xx.
-__device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, float2 Jx, float2 Jy,
-                                             float2 dxr,
-                                             float2 dyr, float2 dxjx, float2 dyjx, float2 dxjy,
-                                             float2 dyjy, float2 dxpxx, float2 dxpxy,
-                                             float2 dypxy, float2 dypyy, float2 a_e, float2 a_xx,
-                                             float2 hf_x, float2 hf_y, float2 g[9]) {
-    const float2 nuy = mul2(uy, sp(-1.f));
-    const float2 uxx = mul2(ux, ux), uyy = mul2(uy, uy), uxy = mul2(ux, uy);
-    const float2 u2 = add2(uxx, uyy);
-    const float2 mx = add2(dxpxx, dypxy);
-    const float2 my = add2(dxpxy, dypyy);
-    // theta_E = (2 + 6 u^2)(d.J) - 2 (u . grad rho)
-    const float2 udr = fma2(uy, dyr, mul2(ux, dxr));
-    const float2 th_e = fma2(sp(-2.f), udr, mul2(fma2(sp(6.f), u2, sp(2.f)), add2(dxjx, dyjy)));
-    // theta_XX = 2/3 ((dxJx - dyJy) - (ux dxr - uy dyr)) - 2 (ux mx - uy my)
-    const float2 b = sub2(sub2(dxjx, dyjy), fma2(ux, dxr, mul2(nuy, dyr)));
-    const float2 th_xx = fma2(sp(2.f / 3.f), b, mul2(sp(-2.f), fma2(ux, mx, mul2(nuy, my))));
-    // theta_XY = 1/3 ((dxJy + dyJx) - (ux dyr + uy dxr)) - (ux my + uy mx)
-    const float2 c = sub2(add2(dxjy, dyjx), fma2(ux, dyr, mul2(uy, dxr)));
-    const float2 th_xy = sub2(mul2(sp(1.f / 3.f), c), fma2(ux, my, mul2(uy, mx)));
-    const float2 ru2 = fma2(dr, u2, u2);
-    const float2 dxx = sub2(uxx, uyy);
-    const float2 e = fma2(sp(-2.f), dr, fma2(sp(3.f), ru2, mul2(a_e, th_e)));
-    const float2 xx = fma2(a_xx, th_xx, fma2(dr, dxx, dxx));
-    const float2 xy = fma2(a_xx, th_xy, fma2(dr, uxy, uxy));
-    const float2 ep = fma2(sp(-3.f), ru2, dr);
-    populations2(dr, add2(Jx, hf_x), add2(Jy, hf_y), Jx, Jy, e, xx, xy, ep, g);
-}
-
 // Per-lane gather state, in column pairs: destination row c (partial, "A")
 // and c + 1 (contribution of row c's upward populations, "U").
 struct Acc {
@@ -255,46 +280,27 @@ struct Acc {
     float2 us[2], ud[2];         // row c + 1: sum and x-difference of g2, g5, g6
 };
 
-template <typename T>
-__device__ __forceinline__ void load4(const T* p, float2 v[2]) {
-    float f[4];
-    Vec4<T>::load(p, f);
-    v[0] = make_float2(f[0], f[1]);
-    v[1] = make_float2(f[2], f[3]);
-}
-
-template <typename T>
-__device__ __forceinline__ void store4(T* p, const float2 v[2]) {
-    const float f[4] = {v[0].x, v[0].y, v[1].x, v[1].y};
-    Vec4<T>::store(p, f);
-}
-
-// Per-item constants of a warp.
-struct Item {
-    int strip0, yb, ye, row_first, nrows;
-    Cols cols;
-};
-
-template <int R, typename T>
+template <int R, bool FORCE, typename T>
 struct RowStep {
     // Field row k of the item: wait for it, read it, update the y window and
     // reconstruct the centre row c = row k - R; close and store row c - 1.
     static __device__ __forceinline__ void run(const StreamArgs& a, const Ring<T>& ring,
-                                               const Item& it, int lane, int k, uint32_t load_no,
-                                               Win& fm2, Win& fm1, Win& dm3, Win& dm2, Acc& acc,
-                                               bool& ok, uint32_t& issued, int& next_load_row) {
-        const int slot = load_no % kSlots;
-        const uint32_t phase = (load_no / kSlots) & 1u;
-        const bool landed = __all_sync(kFull, mbar_wait_bounded(&ring.bars[slot], phase));
+                                               const Item& it, int lane, int k, Win& fm2,
+                                               Win& fm1, Win& dm3, Win& dm2, Acc& acc,
+                                               bool& ok) {
+        const uint32_t pos = it.base + k;
+        const int slot = pos & kSlotMask;
+        const bool landed =
+            __all_sync(kFull, mbar_wait_bounded(&ring.bars[slot], (pos / kSlots) & 1u));
         if (!landed) {
             ok = false;
             return;
         }
         const int col = 4 + 4 * lane;  // slot column of this lane's first column
         float2 nr[2], nux[2], nuy[2];
-        load4<T>(slot_field(ring, slot, 0) + col, nr);
-        load4<T>(slot_field(ring, slot, 1) + col, nux);
-        load4<T>(slot_field(ring, slot, 2) + col, nuy);
+        Vec4<T>::load(slot_field(ring, slot, 0) + col, nr);
+        Vec4<T>::load(slot_field(ring, slot, 1) + col, nux);
+        Vec4<T>::load(slot_field(ring, slot, 2) + col, nuy);
         Win nw;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -307,17 +313,17 @@ struct RowStep {
         }
         // centre row c = r - R from its ring slot (still resident); before
         // the window is full the centre row does not exist yet
-        const int cslot = (load_no + kSlots - R) % kSlots;
+        const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
         if (k >= R) {
-            if (R == 2) load4<T>(slot_field(ring, cslot, 0) + col, cdr);
-            load4<T>(slot_field(ring, cslot, 1) + col, cux);
-            load4<T>(slot_field(ring, cslot, 2) + col, cuy);
+            if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
+            Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
+            Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
         }
         // Five points: the centre row's fields are rebuilt from the ring
-        // (only the differences d1 are held in registers).  Three points:
-        // the centre row is held (fm1).
+        // (only the differences are held in registers).  Three points: the
+        // centre row is held (fm1).
         Win rebuilt;
         if (R == 2) {
 #pragma unroll
@@ -357,16 +363,13 @@ struct RowStep {
         deriv_x<R>(pxx, dxpxx);
         deriv_x<R>(cen.v[W_PXY], dxpxy);
 
-        const float sc = (R == 1) ? 0.5f : 0.125f;
-        const float2 a_e = sp(a.c.a_e * sc), a_xx = sp(a.c.a_xx * sc);
-        const float2 hf_x = sp(0.5f * a.c.fx), hf_y = sp(0.5f * a.c.fy);
         float2 g[2][9];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-            reconstruct2(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h], dxr[h],
-                         dy.v[W_R][h], dxjx[h],
-                         dy.v[W_JX][h], dxjy[h], dy.v[W_JY][h], dxpxx[h], dxpxy[h],
-                         dy.v[W_PXY][h], dy.v[W_PYY][h], a_e, a_xx, hf_x, hf_y, g[h]);
+            reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
+                                dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
+                                dy.v[W_JY][h], dxpxx[h], dxpxy[h], dy.v[W_PXY][h],
+                                dy.v[W_PYY][h], a.k, g[h]);
 
         // populations crossing lane boundaries: right-going (1, 5, 8) of
         // column 3 to the next lane, left-going (3, 6, 7) of column 0 back
@@ -384,13 +387,7 @@ struct RowStep {
         const float2 p6[2] = {make_float2(g[0][6].y, g[1][6].x), make_float2(g[1][6].y, in6)};
         const float2 p7[2] = {make_float2(g[0][7].y, g[1][7].x), make_float2(g[1][7].y, in7)};
 
-        // destination row c - 1 is complete once row c's downward
-        // populations arrive; c is the centre row
-        const int c_row = it.row_first + k - R;
-        const bool store = (c_row - 1 >= it.yb) && (c_row - 1 < it.ye) && lane >= 1 &&
-                           lane <= 30 && (it.strip0 - 4 + 4 * lane) < a.nx;
         float2 odr[2], oux[2], ouy[2];
-        const float2 hfx = sp(0.5f * a.c.fx), hfy = sp(0.5f * a.c.fy);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float2 ss = add2(g[h][0], add2(p1[h], p3[h])), ds = sub2(p1[h], p3[h]);
@@ -398,8 +395,12 @@ struct RowStep {
             const float2 sd = add2(g[h][4], add2(p7[h], p8[h])), dd = sub2(p8[h], p7[h]);
             // close row c - 1: u = J - J dr / (1 + dr)
             const float2 drn = add2(acc.ar[h], sd);
-            const float2 px = add2(add2(acc.ax[h], dd), hfx);
-            const float2 py = add2(sub2(acc.ay[h], sd), hfy);
+            float2 px = add2(acc.ax[h], dd);
+            float2 py = sub2(acc.ay[h], sd);
+            if (FORCE) {
+                px = add2(px, sp(a.k.hfx));
+                py = add2(py, sp(a.k.hfy));
+            }
             const float2 nrho = fma2(drn, sp(-1.f), sp(-1.f));  // -(1 + dr)
             const float2 ninv = make_float2(rcp_approx(nrho.x), rcp_approx(nrho.y));
             odr[h] = drn;
@@ -412,36 +413,27 @@ struct RowStep {
             acc.us[h] = su;
             acc.ud[h] = du;
         }
-        if (store) {
+        // destination row c - 1 = yb + k - 2R - 2 is an output row from k = 2R + 2
+        if (k >= 2 * R + 2 && it.lane_stores) {
             T* dst = static_cast<T*>(a.dst);
-            const size_t o = (size_t)(c_row - 1) * a.pitch + (it.strip0 - 4 + 4 * lane);
-            store4<T>(dst + o, odr);
-            store4<T>(dst + a.plane + o, oux);
-            store4<T>(dst + 2 * a.plane + o, ouy);
+            const size_t o =
+                (size_t)(it.yb + k - 2 * R - 2) * a.pitch + (it.strip0 - 4 + 4 * lane);
+            Vec4<T>::store(dst + o, odr);
+            Vec4<T>::store(dst + a.plane + o, oux);
+            Vec4<T>::store(dst + 2 * a.plane + o, ouy);
         }
-
         // rotate the window: the oldest row/difference take the new ones
         if (R == 1) fm2 = nw;
         if (R == 2) dm3 = d1new;
-
-        // the centre row's slot is no longer needed: refill it with the row
-        // kSlots ahead
-        __syncwarp();
-        if (k >= R && k - R + kSlots < it.nrows) {
-            issue_row<T>(a, ring, cslot, next_load_row, it.cols, lane);
-            next_load_row = next_row(next_load_row, a.ny);
-            ++issued;
-        }
     }
 };
 
-template <int R, typename T>
+template <int R, bool FORCE, typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
     fd_step_stream_kernel(StreamArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t slot_bytes = (size_t)3 * kLoadCols * sizeof(T);
-    const size_t warp_bytes = kSlots * slot_bytes;
+    const int warp_bytes = kSlots * 3 * kLoadCols * (int)sizeof(T);
     Ring<T> ring;
     ring.slot_base = reinterpret_cast<T*>(smem + warp * warp_bytes);
     ring.bars = reinterpret_cast<uint64_t*>(smem + kWarpsPerBlock * warp_bytes) + warp * kSlots;
@@ -451,9 +443,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
     }
     __syncwarp();
 
-    uint32_t loads = 0;   // rows consumed by this warp in finished items (ring position)
-    uint32_t issued = 0;  // row copies issued by this warp
-    uint32_t consumed = 0;
+    uint32_t base = 0;      // ring position of the current item's row 0
+    uint32_t issued = 0;    // ring positions issued so far
+    uint32_t consumed = 0;  // ring positions waited for so far
     bool ok = true;
     for (int item = blockIdx.x * kWarpsPerBlock + warp; item < a.nitems && ok;
          item += gridDim.x * kWarpsPerBlock) {
@@ -464,45 +456,51 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
         it.ye = min(a.ny, it.yb + a.seg_rows);
         it.row_first = it.yb - 1 - R;
         it.nrows = it.ye - it.yb + 2 + 2 * R;
-        it.cols = strip_cols(a, it.strip0);
-        int next_load_row = wrap_index(it.row_first, a.ny);
-        const int prologue = min(kSlots, it.nrows);
-        for (int k = 0; k < prologue; ++k) {
-            issue_row<T>(a, ring, (loads + k) % kSlots, next_load_row, it.cols, lane);
-            next_load_row = next_row(next_load_row, a.ny);
-        }
-        issued += prologue;
+        it.x0 = wrap_index(it.strip0 - 8, a.nx);
+        it.first = min(kLoadCols, a.nx - it.x0);
+        it.lane_stores = lane >= 1 && lane <= 30 && (it.strip0 - 4 + 4 * lane) < a.nx;
+        it.base = base;
+        // every lane is done with the slots of the previous item
         __syncwarp();
+        // prologue: the first kSlots rows, two per issue
+        for (int k0 = 0; k0 < kSlots && k0 < it.nrows; k0 += 2)
+            issue_rows<T>(a, ring, it, k0, min(2, it.nrows - k0), lane);
+        issued = base + min(kSlots, it.nrows);
         Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
         Acc acc = {};
         int k = 0;
         for (; k + 1 < it.nrows; k += 2) {
-            RowStep<R, T>::run(a, ring, it, lane, k, loads + k, w0, w1, w2, w3, acc, ok, issued,
-                               next_load_row);
+            RowStep<R, FORCE, T>::run(a, ring, it, lane, k, w0, w1, w2, w3, acc, ok);
+            if (!ok) break;
+            RowStep<R, FORCE, T>::run(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc, ok);
             if (!ok) {
-                consumed = loads + k;
+                ++k;
                 break;
             }
-            RowStep<R, T>::run(a, ring, it, lane, k + 1, loads + k + 1, w1, w0, w3, w2, acc, ok,
-                               issued, next_load_row);
-            if (!ok) {
-                consumed = loads + k + 1;
-                break;
+            // the centre rows of these two steps (k - R, k + 1 - R) are no
+            // longer needed: refill their slots with the rows kSlots ahead
+            __syncwarp();
+            const int m1 = k + 1 - R;
+            const int n0 = (int)(issued - base);
+            const int cnt = min(m1 + kSlots + 1, it.nrows) - n0;
+            if (m1 >= 0 && cnt > 0) {
+                issue_rows<T>(a, ring, it, n0, cnt, lane);
+                issued += cnt;
             }
         }
         if (ok && k < it.nrows) {
-            RowStep<R, T>::run(a, ring, it, lane, k, loads + k, w0, w1, w2, w3, acc, ok, issued,
-                               next_load_row);
-            if (!ok) consumed = loads + k;
+            RowStep<R, FORCE, T>::run(a, ring, it, lane, k, w0, w1, w2, w3, acc, ok);
+            if (ok) ++k;
         }
-        loads += it.nrows;
+        consumed = base + k;
+        base += it.nrows;
     }
     if (!ok) {
         // A copy did not complete in time: record it, then give every copy
         // still in flight a bounded chance to land before the CTA exits.
         if (lane == 0) atomicExch(a.status, FDLBM_ERR_TIMEOUT);
         for (uint32_t n = consumed; n < issued; ++n)
-            mbar_wait_bounded(&ring.bars[n % kSlots], (n / kSlots) & 1u);
+            mbar_wait_bounded(&ring.bars[n & kSlotMask], (n / kSlots) & 1u);
     }
 }
 
@@ -537,22 +535,17 @@ Plan make_plan(int nx, int ny, int R, int resident_warps) {
     return best;
 }
 
-template <int R, typename T>
+template <int R, bool FORCE, typename T>
 cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
+    auto kernel = fd_step_stream_kernel<R, FORCE, T>;
     const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(T) + kSlots * 8);
-    static bool attr_set = false;  // per template instance; set once per process
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fd_step_stream_kernel<R, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     if (h->stream_plan_warps == 0) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fd_step_stream_kernel<R, T>,
-                                                      kWarpsPerBlock * 32, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerBlock * 32, smem);
         h->stream_plan_warps = std::max(1, sms * per_sm * kWarpsPerBlock);
     }
     const Plan plan = make_plan(h->p.nx, h->p.ny, R, h->stream_plan_warps);
@@ -567,20 +560,31 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     a.seg_rows = plan.seg_rows;
     a.nsegs = plan.nsegs;
     a.nitems = plan.nitems;
-    a.c.a_e = (float)(1.0 - 1.0 / h->p.s_e);
-    a.c.a_xx = (float)(1.0 - 1.0 / h->p.s_xx);
-    a.c.fx = (float)h->p.force_x;
-    a.c.fy = (float)h->p.force_y;
-    a.c.xi = (float)h->p.wall_xi;
+    const double sc = (R == 1) ? 0.5 : 0.125;  // derivatives are computed times 2 or 8
+    const double ae = (1.0 - 1.0 / h->p.s_e) * sc / 36.0;
+    const double axx = (1.0 - 1.0 / h->p.s_xx) * sc;
+    a.k.e6 = (float)(6.0 * ae);
+    a.k.e2 = (float)(2.0 * ae);
+    a.k.em2 = (float)(-2.0 * ae);
+    a.k.x23 = (float)(2.0 / 3.0 * axx);
+    a.k.xm2 = (float)(-2.0 * axx);
+    a.k.x13 = (float)(axx / 3.0);
+    a.k.xm1 = (float)(-axx);
+    a.k.hfx = (float)(0.5 * h->p.force_x);
+    a.k.hfy = (float)(0.5 * h->p.force_y);
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
-    fd_step_stream_kernel<R, T><<<plan.blocks, kWarpsPerBlock * 32, smem, h->stream>>>(a);
+    kernel<<<plan.blocks, kWarpsPerBlock * 32, smem, h->stream>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_stream_stencil(fdlbm_s* h, const void* src, void* dst) {
-    if (h->p.scheme == FDLBM_SCHEME_FD3) return launch_stream_typed<1, T>(h, src, dst);
-    return launch_stream_typed<2, T>(h, src, dst);
+    const bool force = h->p.force_x != 0.0 || h->p.force_y != 0.0;
+    if (h->p.scheme == FDLBM_SCHEME_FD3)
+        return force ? launch_stream_typed<1, true, T>(h, src, dst)
+                     : launch_stream_typed<1, false, T>(h, src, dst);
+    return force ? launch_stream_typed<2, true, T>(h, src, dst)
+                 : launch_stream_typed<2, false, T>(h, src, dst);
 }
 
 }  // namespace

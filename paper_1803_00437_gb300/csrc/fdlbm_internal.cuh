@@ -12,7 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/fdlbm.h"
+#include "fdlbm.h"  // include/ of the repository (-I)
 
 namespace fdlbm {
 
