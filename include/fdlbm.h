@@ -159,6 +159,40 @@ int fdlbm_moments_host(fdlbm_t* h, float* drho, float* ux, float* uy);
 #define FDLBM_REDUCE_MAXABS 4
 int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out);
 
+/* fdlbm_reduce_fields_static -- the reductions of fdlbm_reduce for callers
+ * that cannot allocate device memory.
+ *
+ * The paper has no counterpart; this is a convenience of the library.  Some
+ * callers may not call cudaMalloc at all (code that runs inside a memory
+ * pool it does not own, a plug-in that is only handed the buffers it must
+ * fill, a region being captured into a CUDA graph), so they cannot provide
+ * the workspace that fdlbm_create needs.  This entry point takes fields they
+ * already hold on the device -- drho, ux, uy, nx*ny floats each, row-major,
+ * for instance written by fdlbm_moments -- and computes the same FP64 sums
+ * as fdlbm_reduce without any handle, workspace or allocation.
+ *
+ *   what, args: as for fdlbm_reduce (FDLBM_REDUCE_*; args = (m, n) for MODE).
+ *   out: DEVICE pointer to 4 doubles, written asynchronously on `stream`:
+ *        out[0..1] as fdlbm_reduce's out, out[2] = 0, out[3] = number of
+ *        nodes holding a non-finite value (the caller checks it).
+ *   stream: a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Scratch: the per-block partial sums live in one fixed 32 KiB device array
+ * inside the library; every GPU on which the library is loaded keeps it
+ * until the process exits.  The first call on each device looks up that
+ * array's device address (cudaGetSymbolAddress), so make the first call on a
+ * device before capturing its stream into a CUDA graph.  All calls on a
+ * device share the array and it keeps the last call's contents: calls
+ * ordered on one stream are correct, calls that overlap on the GPU (other
+ * streams, unordered host threads) race on it and give wrong results.
+ * Limits: nx, ny >= 1 and nx*ny <= FDLBM_STATIC_REDUCE_MAX_NODES; anything
+ * else returns FDLBM_ERR_INVALID before any work is enqueued.  Returns
+ * FDLBM_ERR_CUDA if a launch fails.  Never calls cudaMalloc or cudaFree. */
+#define FDLBM_STATIC_REDUCE_MAX_NODES (1LL << 30)
+int fdlbm_reduce_fields_static(const float* drho, const float* ux, const float* uy, int32_t nx,
+                               int32_t ny, int32_t what, const double* args, double* out,
+                               void* stream);
+
 /* Wait for all work enqueued by this handle. */
 int fdlbm_sync(fdlbm_t* h);
 

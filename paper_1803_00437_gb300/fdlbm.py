@@ -83,6 +83,9 @@ def load_library(path: str | None = None):
         L.fdlbm_status_string.restype = cp
         L.fdlbm_launch_count.argtypes = [vp]
         L.fdlbm_launch_count.restype = ctypes.c_int64
+        L.fdlbm_reduce_fields_static.argtypes = [fp, fp, fp, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32, fp, fp, vp]
+        L.fdlbm_reduce_fields_static.restype = ctypes.c_int
         for name in ("fdlbm_create", "fdlbm_set_stream", "fdlbm_init", "fdlbm_init_host",
                      "fdlbm_init_modes", "fdlbm_step", "fdlbm_moments", "fdlbm_moments_host",
                      "fdlbm_reduce", "fdlbm_sync"):
@@ -275,3 +278,29 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+def reduce_fields_static(drho, ux, uy, what: str, args=None, out=None, stream=None):
+    """fdlbm_reduce_fields_static: FP64 reductions of device fields (float32
+    CUDA tensors [ny, nx]) without a handle or workspace.  Returns the device
+    tensor `out` (4 doubles: results, 0, count of non-finite nodes); the work
+    is asynchronous on `stream` (default: the current stream)."""
+    import torch
+    lib = load_library()
+    ny, nx = drho.shape
+    for t in (drho, ux, uy):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and tuple(t.shape) == (ny, nx)):
+            raise ValueError("fields must be contiguous float32 CUDA tensors of one shape")
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=drho.device)
+    a = None if args is None else np.ascontiguousarray(args, dtype=np.float64)
+    s = stream if stream is not None else torch.cuda.current_stream(drho.device)
+    rc = lib.fdlbm_reduce_fields_static(
+        ctypes.c_void_p(drho.data_ptr()), ctypes.c_void_p(ux.data_ptr()),
+        ctypes.c_void_p(uy.data_ptr()), int(nx), int(ny), REDUCE[what],
+        ctypes.c_void_p(a.ctypes.data) if a is not None else None,
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if rc != OK:
+        raise FdlbmError(rc, f"fdlbm_reduce_fields_static({what}): {status_string(rc)}")
+    return out
