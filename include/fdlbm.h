@@ -159,6 +159,67 @@ int fdlbm_moments_host(fdlbm_t* h, float* drho, float* ux, float* uy);
 #define FDLBM_REDUCE_MAXABS 4
 int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out);
 
+/* ---- batches of lattices ------------------------------------------------------
+ *
+ * Many independent lattices (periodic, or channels with walls in y) of any
+ * size (16 <= nx, ny <= max_side), each with its own relaxation rates and
+ * force, stepped together by one persistent FD-LBM kernel per step (the
+ * scheme of Sec. 2 with the streaming data path); runs of up to 64 steps are
+ * captured once in a CUDA graph and replayed.  FP32 storage.  Slots are
+ * added and removed between calls (continuous batching); each slot's state
+ * lives in a caller-owned arena with 8 periodic ghost columns per row side.
+ * Results equal those of a single-lattice handle with the same parameters
+ * up to FP32 rounding. */
+typedef struct fdlbm_batch_s fdlbm_batch_t;
+
+typedef struct fdlbm_batch_params {
+    int32_t scheme;        /* FDLBM_SCHEME_FD3 or FDLBM_SCHEME_FD5 (all slots)      */
+    int32_t max_lattices;  /* number of slots                                      */
+    int64_t arena_bytes;   /* device bytes for the slots' states (2 copies each)   */
+    int32_t max_side;      /* largest nx or ny of a slot (sizes work lists, staging) */
+    int32_t flags;         /* must be 0                                            */
+} fdlbm_batch_params;
+
+/* Workspace bytes for a batch (arena + descriptors + work list + staging),
+ * 0 if the parameters are invalid. */
+size_t fdlbm_batch_workspace_size(const fdlbm_batch_params* bp);
+
+/* Create a batch on the current device; workspace is caller-owned device
+ * memory (256-byte aligned, fdlbm_batch_workspace_size bytes), kept until
+ * fdlbm_batch_destroy; stream: a cudaStream_t. */
+int fdlbm_batch_create(const fdlbm_batch_params* bp, void* workspace, size_t workspace_bytes,
+                       void* stream, fdlbm_batch_t** out);
+void fdlbm_batch_destroy(fdlbm_batch_t* b);
+
+/* Reserve a slot for a lattice (p->scheme must be the batch's, storage F32);
+ * *slot receives its index.  FDLBM_ERR_NOMEM if no slot or arena space. */
+int fdlbm_batch_add(fdlbm_batch_t* b, const fdlbm_params* p, int32_t* slot);
+/* Release a slot and its arena space. */
+int fdlbm_batch_remove(fdlbm_batch_t* b, int32_t slot);
+/* Initial state of a slot from device fields (as fdlbm_init) or modes (as
+ * fdlbm_init_modes). */
+int fdlbm_batch_init(fdlbm_batch_t* b, int32_t slot, const float* drho, const float* ux,
+                     const float* uy);
+int fdlbm_batch_init_modes(fdlbm_batch_t* b, int32_t slot, int32_t n_modes, const double* modes,
+                           double mean_ux, double mean_uy);
+/* Advance every slot by nsteps, or slot s by min(slot_steps[s], nsteps) when
+ * slot_steps (host array of max_lattices counts) is given. */
+int fdlbm_batch_step(fdlbm_batch_t* b, int64_t nsteps, const int64_t* slot_steps);
+/* A slot's drho, ux, uy into device arrays (nx*ny floats each). */
+int fdlbm_batch_moments(fdlbm_batch_t* b, int32_t slot, float* drho, float* ux, float* uy);
+/* FP64 reductions of one slot, as fdlbm_reduce (host out; waits). */
+int fdlbm_batch_reduce(fdlbm_batch_t* b, int32_t slot, int32_t what, const double* args,
+                       double* out);
+/* Wait for the batch's stream; reports a device-side timeout. */
+int fdlbm_batch_sync(fdlbm_batch_t* b);
+/* Tuning knobs (chosen by the autotuner in the Python layer): rows per work
+ * item (>= 8) and persistent CTAs (0 = one wave of resident CTAs). */
+int fdlbm_batch_set_segment_rows(fdlbm_batch_t* b, int32_t rows);
+int fdlbm_batch_set_grid(fdlbm_batch_t* b, int32_t ctas);
+const char* fdlbm_batch_last_error(const fdlbm_batch_t* b);
+int64_t fdlbm_batch_launch_count(const fdlbm_batch_t* b);
+int32_t fdlbm_batch_count(const fdlbm_batch_t* b);
+
 /* fdlbm_reduce_fields_static -- the reductions of fdlbm_reduce for callers
  * that cannot allocate device memory.
  *

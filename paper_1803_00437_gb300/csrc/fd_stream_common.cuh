@@ -1,0 +1,191 @@
+// fd_stream_common.cuh -- device code shared by the streaming FD-LBM kernels
+// (single lattice and batched): paired FP32 arithmetic on column pairs,
+// 4-column vector access in each storage type, x-derivatives by warp
+// shuffles and the reconstruction of Sec. 2 in deviation form.
+#pragma once
+
+#include "fd_common.cuh"
+
+namespace fdlbm {
+namespace stream {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- paired FP32 arithmetic (two lattice columns per instruction) --------------
+
+__device__ __forceinline__ float2 sp(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
+// Hardware reciprocal (relative error ~2^-23).  Used only where it scales a
+// small correction term, so its error is far below FP32 resolution.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---- storage of 4 consecutive columns ----------------------------------------------
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float2 v[2]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = make_float2(q.x, q.y);
+        v[1] = make_float2(q.z, q.w);
+    }
+    static __device__ __forceinline__ void store(float* p, const float2 v[2]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+};
+template <>
+struct Vec4<__half> {
+    static __device__ __forceinline__ void load(const __half* p, float2 v[2]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        v[1] = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    }
+    static __device__ __forceinline__ void store(__half* p, const float2 v[2]) {
+        __half2 a = __float22half2_rn(v[0]), b = __float22half2_rn(v[1]);
+        uint2 q;
+        q.x = *reinterpret_cast<uint32_t*>(&a);
+        q.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+template <>
+struct Vec4<__nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, float2 v[2]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        v[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, const float2 v[2]) {
+        __nv_bfloat162 a = __float22bfloat162_rn(v[0]), b = __float22bfloat162_rn(v[1]);
+        uint2 q;
+        q.x = *reinterpret_cast<uint32_t*>(&a);
+        q.y = *reinterpret_cast<uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = q;
+    }
+};
+
+// Fields of the y window: rho - 1, Jx, Jy, Jx Jy / rho, Jy Jy / rho, each as
+// two column pairs: v[f][0] = columns (0, 1), v[f][1] = columns (2, 3).
+enum { W_R = 0, W_JX, W_JY, W_PXY, W_PYY, W_N };
+
+struct Win {
+    float2 v[W_N][2];
+};
+
+// Relaxation factors with the derivative scale (2 or 8) and the constants
+// of theta and of M^-1 folded in (see reconstruct2).
+struct StreamCoeffs {
+    float e6, e2, em2;         // theta_E terms, times (1 - 1/s_e) / (36 scale)
+    float x23, xm2, x13, xm1;  // theta_XX, theta_XY terms, times (1 - 1/s_xx) / scale
+    float hfx, hfy;            // half of the body force
+};
+
+// x-derivative (scaled by 2 or 8) at the 4 columns of this lane.
+template <int R>
+__device__ __forceinline__ void deriv_x(const float2 v[2], float2 d[2]) {
+    const float f0 = v[0].x, f1 = v[0].y, f2 = v[1].x, f3 = v[1].y;
+    const float l1 = __shfl_up_sync(kFull, f3, 1);
+    const float r0 = __shfl_down_sync(kFull, f0, 1);
+    if (R == 1) {
+        // 2 d/dx = f(+1) - f(-1)
+        d[0] = make_float2(f1 - l1, f2 - f0);
+        d[1] = make_float2(f3 - f1, r0 - f2);
+    } else {
+        // 8 d/dx = 6 (f(+1) - f(-1)) - (f(+2) - f(-2))
+        const float l2 = __shfl_up_sync(kFull, f2, 1);
+        const float r1 = __shfl_down_sync(kFull, f1, 1);
+        d[0] = fma2(sp(6.f), make_float2(f1 - l1, f2 - f0), make_float2(l2 - f2, l1 - f3));
+        d[1] = fma2(sp(6.f), make_float2(f3 - f1, r0 - f2), make_float2(f0 - r0, f1 - r1));
+    }
+}
+
+// Reconstruction (Sec. 2) of two columns, g_a = f*_a - w_a, from scaled
+// derivatives.  With K_E = (1 - 1/s_e) theta_E, K_XX, K_XY likewise and
+// u2 = |u|^2, the moments of the table of Sec. 2 substituted into M^-1 give
+//   g0 = dr - 4 (axis + diag)            (so that sum g = dr, unbiased)
+//   axis = dr/9 + rho u2/12 - K_E/36,     diag = dr/36 + rho u2/12 + K_E/18
+//   tx = (jx + Jx)/6, sx = (jx - 2 tx)/4 (so that sum c g = jx, unbiased)
+//   g1,3 = axis + XX/4 +- tx,  g2,4 = axis - XX/4 +- ty,
+//   g5,7 = diag + XY/4 +- (sx + sy),  g6,8 = diag - XY/4 +- (sy - sx),
+// with jx = Jx + F/2 (Strang) and q = -J, epsilon at equilibrium.
+template <bool FORCE>
+__device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, float2 Jx, float2 Jy,
+                                             float2 dxr, float2 dyr, float2 dxjx, float2 dyjx,
+                                             float2 dxjy, float2 dyjy, float2 dxpxx,
+                                             float2 dxpxy, float2 dypxy, float2 dypyy,
+                                             const StreamCoeffs& k, float2 g[9]) {
+    const float2 nuy = mul2(uy, sp(-1.f));
+    const float2 uxx = mul2(ux, ux), uyy = mul2(uy, uy), uxy = mul2(ux, uy);
+    const float2 u2 = add2(uxx, uyy);
+    const float2 mx = add2(dxpxx, dypxy);
+    const float2 my = add2(dxpxy, dypyy);
+    // K_E / 36 = a_e [(2 + 6 u^2)(d.J) - 2 (u . grad rho)] / 36
+    const float2 udr = fma2(uy, dyr, mul2(ux, dxr));
+    const float2 ke36 =
+        fma2(sp(k.em2), udr, mul2(fma2(sp(k.e6), u2, sp(k.e2)), add2(dxjx, dyjy)));
+    // K_XX = a_xx [2/3 ((dxJx - dyJy) - (ux dxr - uy dyr)) - 2 (ux mx - uy my)]
+    const float2 b = sub2(sub2(dxjx, dyjy), fma2(ux, dxr, mul2(nuy, dyr)));
+    const float2 kxx = fma2(sp(k.x23), b, mul2(sp(k.xm2), fma2(ux, mx, mul2(nuy, my))));
+    // K_XY = a_xx [1/3 ((dxJy + dyJx) - (ux dyr + uy dxr)) - (ux my + uy mx)]
+    const float2 c = sub2(add2(dxjy, dyjx), fma2(ux, dyr, mul2(uy, dxr)));
+    const float2 kxy = fma2(sp(k.x13), c, mul2(sp(k.xm1), fma2(ux, my, mul2(uy, mx))));
+    // equilibrium parts: rho u2, rho (ux^2 - uy^2), rho ux uy
+    const float2 ru2_12 = mul2(fma2(dr, u2, u2), sp(1.f / 12.f));
+    const float2 dxx = sub2(uxx, uyy);
+    const float2 xx = add2(fma2(dr, dxx, dxx), kxx);
+    const float2 xy = add2(fma2(dr, uxy, uxy), kxy);
+    const float2 axis = sub2(fma2(dr, sp(1.f / 9.f), ru2_12), ke36);
+    const float2 diag = fma2(sp(2.f), ke36, fma2(dr, sp(1.f / 36.f), ru2_12));
+    g[0] = fma2(sp(-4.f), add2(axis, diag), dr);
+    float2 tx, ty, jx = Jx, jy = Jy;
+    if (FORCE) {
+        jx = add2(Jx, sp(k.hfx));
+        jy = add2(Jy, sp(k.hfy));
+        tx = mul2(add2(jx, Jx), sp(1.f / 6.f));
+        ty = mul2(add2(jy, Jy), sp(1.f / 6.f));
+    } else {
+        tx = mul2(Jx, sp(1.f / 3.f));
+        ty = mul2(Jy, sp(1.f / 3.f));
+    }
+    const float2 sx = mul2(fma2(sp(-2.f), tx, jx), sp(0.25f));
+    const float2 sy = mul2(fma2(sp(-2.f), ty, jy), sp(0.25f));
+    const float2 ax = fma2(xx, sp(0.25f), axis), ay = fma2(xx, sp(-0.25f), axis);
+    const float2 dp = fma2(xy, sp(0.25f), diag), dm = fma2(xy, sp(-0.25f), diag);
+    const float2 spp = add2(sx, sy), smm = sub2(sy, sx);
+    g[1] = add2(ax, tx);
+    g[3] = sub2(ax, tx);
+    g[2] = add2(ay, ty);
+    g[4] = sub2(ay, ty);
+    g[5] = add2(dp, spp);
+    g[7] = sub2(dp, spp);
+    g[6] = add2(dm, smm);
+    g[8] = sub2(dm, smm);
+}
+
+// Per-lane gather state, in column pairs: destination row c (partial, "A")
+// and c + 1 (contribution of row c's upward populations, "U").
+struct Acc {
+    float2 ar[2], ax[2], ay[2];  // row c: rho - 1, Jx, Jy (missing row c + 1)
+    float2 us[2], ud[2];         // row c + 1: sum and x-difference of g2, g5, g6
+};
+
+
+}  // namespace stream
+}  // namespace fdlbm

@@ -45,6 +45,14 @@ class Params(ctypes.Structure):
     ]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [
+        ("scheme", ctypes.c_int32), ("max_lattices", ctypes.c_int32),
+        ("arena_bytes", ctypes.c_int64), ("max_side", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -83,6 +91,34 @@ def load_library(path: str | None = None):
         L.fdlbm_status_string.restype = cp
         L.fdlbm_launch_count.argtypes = [vp]
         L.fdlbm_launch_count.restype = ctypes.c_int64
+        bp = ctypes.POINTER(BatchParams)
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        L.fdlbm_batch_workspace_size.argtypes = [bp]
+        L.fdlbm_batch_workspace_size.restype = ctypes.c_size_t
+        L.fdlbm_batch_create.argtypes = [bp, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        L.fdlbm_batch_destroy.argtypes = [vp]
+        L.fdlbm_batch_destroy.restype = None
+        L.fdlbm_batch_add.argtypes = [vp, pp, ctypes.POINTER(i32)]
+        L.fdlbm_batch_remove.argtypes = [vp, i32]
+        L.fdlbm_batch_init.argtypes = [vp, i32, fp, fp, fp]
+        L.fdlbm_batch_init_modes.argtypes = [vp, i32, i32, fp, ctypes.c_double, ctypes.c_double]
+        L.fdlbm_batch_step.argtypes = [vp, i64, fp]
+        L.fdlbm_batch_moments.argtypes = [vp, i32, fp, fp, fp]
+        L.fdlbm_batch_reduce.argtypes = [vp, i32, i32, fp, fp]
+        L.fdlbm_batch_sync.argtypes = [vp]
+        L.fdlbm_batch_set_segment_rows.argtypes = [vp, i32]
+        L.fdlbm_batch_set_grid.argtypes = [vp, i32]
+        L.fdlbm_batch_last_error.argtypes = [vp]
+        L.fdlbm_batch_last_error.restype = cp
+        L.fdlbm_batch_launch_count.argtypes = [vp]
+        L.fdlbm_batch_launch_count.restype = i64
+        L.fdlbm_batch_count.argtypes = [vp]
+        L.fdlbm_batch_count.restype = i32
+        for name in ("fdlbm_batch_create", "fdlbm_batch_add", "fdlbm_batch_remove",
+                     "fdlbm_batch_init", "fdlbm_batch_init_modes", "fdlbm_batch_step",
+                     "fdlbm_batch_moments", "fdlbm_batch_reduce", "fdlbm_batch_sync",
+                     "fdlbm_batch_set_segment_rows", "fdlbm_batch_set_grid"):
+            getattr(L, name).restype = ctypes.c_int
         L.fdlbm_reduce_fields_static.argtypes = [fp, fp, fp, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, fp, fp, vp]
         L.fdlbm_reduce_fields_static.restype = ctypes.c_int
@@ -304,3 +340,166 @@ def reduce_fields_static(drho, ux, uy, what: str, args=None, out=None, stream=No
     if rc != OK:
         raise FdlbmError(rc, f"fdlbm_reduce_fields_static({what}): {status_string(rc)}")
     return out
+
+
+def _mode_records(modes):
+    rec = np.ascontiguousarray(
+        [[float(md[0]), float(md[1]), float(md[2]), float(md[3])] if not hasattr(md, "m")
+         else [float(md.m), float(md.n), float(md.amp), float(md.phase)] for md in modes],
+        dtype=np.float64).reshape(-1)
+    return rec
+
+
+class Batch:
+    """Many independent lattices stepped together (fdlbm_batch_* in the C ABI).
+
+    Slots take LatticeConfig's of the batch's scheme with FP32 storage, any
+    size 16..max_side, periodic or walls in y, each with its own rates and
+    force.  The workspace (arena + tables) is a torch uint8 CUDA tensor."""
+
+    # segment lengths measured best per (device, scheme, size class); filled by tune()
+    _tuned: dict = {}
+
+    def __init__(self, scheme="fd5", max_lattices=64, arena_bytes=1 << 30, max_side=512,
+                 device=None, stream=None):
+        import torch
+        self.lib = load_library()
+        self.scheme = scheme
+        self.bp = BatchParams(SCHEMES[scheme], int(max_lattices), int(arena_bytes),
+                              int(max_side), 0)
+        nbytes = int(self.lib.fdlbm_batch_workspace_size(ctypes.byref(self.bp)))
+        if nbytes == 0:
+            raise FdlbmError(ERR_INVALID, "invalid batch parameters")
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.fdlbm_batch_create(ctypes.byref(self.bp),
+                                             ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                             ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.byref(self._h))
+        if rc != OK:
+            raise FdlbmError(rc, f"fdlbm_batch_create failed: {status_string(rc)}")
+        self.max_lattices = int(max_lattices)
+        self.configs = {}
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = self.lib.fdlbm_batch_last_error(self._h).decode()
+            raise FdlbmError(rc, f"{what}: {status_string(rc)}: {msg}")
+
+    def add(self, cfg: LatticeConfig) -> int:
+        p = cfg.params()
+        slot = ctypes.c_int32()
+        self._check(self.lib.fdlbm_batch_add(self._h, ctypes.byref(p), ctypes.byref(slot)), "add")
+        self.configs[slot.value] = cfg
+        return slot.value
+
+    def remove(self, slot: int):
+        self._check(self.lib.fdlbm_batch_remove(self._h, int(slot)), "remove")
+        self.configs.pop(slot, None)
+
+    def init(self, slot, drho, ux, uy):
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (drho, ux, uy)]
+        self._check(self.lib.fdlbm_batch_init(self._h, int(slot), *ptrs), "init")
+
+    def init_modes(self, slot, modes, mean_velocity=(0.0, 0.0)):
+        rec = _mode_records(modes)
+        ptr = ctypes.c_void_p(rec.ctypes.data) if rec.size else None
+        self._check(self.lib.fdlbm_batch_init_modes(self._h, int(slot), rec.size // 4, ptr,
+                                                    float(mean_velocity[0]),
+                                                    float(mean_velocity[1])), "init_modes")
+
+    def step(self, nsteps: int, slot_steps=None):
+        """Advance every slot by nsteps, or slot s by min(slot_steps[s], nsteps)
+        (slot_steps: dict slot -> steps or an array of max_lattices counts)."""
+        arr = None
+        if slot_steps is not None:
+            arr = np.zeros(self.max_lattices, dtype=np.int64)
+            if isinstance(slot_steps, dict):
+                for k, v in slot_steps.items():
+                    arr[int(k)] = int(v)
+            else:
+                arr[:len(slot_steps)] = np.asarray(slot_steps, dtype=np.int64)
+        self._check(self.lib.fdlbm_batch_step(
+            self._h, int(nsteps), ctypes.c_void_p(arr.ctypes.data) if arr is not None else None),
+            "step")
+
+    def moments(self, slot):
+        import torch
+        cfg = self.configs[slot]
+        out = [torch.empty((cfg.ny, cfg.nx), dtype=torch.float32, device=self.device)
+               for _ in range(3)]
+        self._check(self.lib.fdlbm_batch_moments(
+            self._h, int(slot), *[ctypes.c_void_p(t.data_ptr()) for t in out]), "moments")
+        return tuple(out)
+
+    def reduce(self, slot, what, args=None):
+        out = np.zeros(4, dtype=np.float64)
+        a = None if args is None else np.ascontiguousarray(args, dtype=np.float64)
+        self._check(self.lib.fdlbm_batch_reduce(
+            self._h, int(slot), REDUCE[what], ctypes.c_void_p(a.ctypes.data) if a is not None
+            else None, ctypes.c_void_p(out.ctypes.data)), f"reduce({what})")
+        n = 2 if what in ("momentum", "mode", "maxabs") else 1
+        return out[:n].copy()
+
+    def sync(self):
+        self._check(self.lib.fdlbm_batch_sync(self._h), "sync")
+
+    def set_segment_rows(self, rows: int):
+        self._check(self.lib.fdlbm_batch_set_segment_rows(self._h, int(rows)), "segment rows")
+
+    def set_grid(self, ctas: int):
+        self._check(self.lib.fdlbm_batch_set_grid(self._h, int(ctas)), "grid")
+
+    @property
+    def count(self) -> int:
+        return int(self.lib.fdlbm_batch_count(self._h))
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.fdlbm_batch_launch_count(self._h))
+
+    def _size_class(self):
+        sides = [max(c.nx, c.ny) for c in self.configs.values()] or [0]
+        return int(2 ** round(np.log2(max(16, float(np.mean(sides))))))
+
+    def tune(self, steps: int = 8, candidates=(16, 32, 64, 128, 256)) -> int:
+        """Autotuner: time `steps` steps of the current slots for each row-segment
+        length and keep the fastest (cached per device, scheme and size class).
+        The slots' states advance while tuning: call it before initialising
+        them, or re-initialise afterwards."""
+        import torch
+        key = (torch.cuda.get_device_name(self.device), self.scheme, self._size_class())
+        if key in Batch._tuned:
+            self.set_segment_rows(Batch._tuned[key][0])
+            return Batch._tuned[key][0]
+        timings = {}
+        for rows in candidates:
+            self.set_segment_rows(rows)
+            self.step(1)  # work list and graph for this choice
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.step(steps)
+            e1.record(self.stream)
+            self.sync()
+            timings[rows] = e0.elapsed_time(e1) / steps
+        best = min(timings, key=timings.get)
+        Batch._tuned[key] = (best, timings)
+        self.set_segment_rows(best)
+        return best
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.fdlbm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
