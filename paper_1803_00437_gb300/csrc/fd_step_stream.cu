@@ -75,6 +75,7 @@ struct Item {
     int x0, first;     // staged columns: kLoadCols from x0, wrapping once at nx
     bool lane_stores;  // this lane's 4 columns are output columns
     uint32_t base;     // ring position of the item's row 0
+    size_t out;        // element offset of this lane's columns in output row yb
 };
 
 // Issue rows k0 .. k0 + count - 1 (count 1 or 2) of the item into their ring
@@ -241,12 +242,10 @@ struct RowStep {
         }
         // destination row c - 1 = yb + k - 2R - 2 is an output row from k = 2R + 2
         if (k >= 2 * R + 2 && it.lane_stores) {
-            T* dst = static_cast<T*>(a.dst);
-            const size_t o =
-                (size_t)(it.yb + k - 2 * R - 2) * a.pitch + (it.strip0 - 4 + 4 * lane);
-            Vec4<T>::store(dst + o, odr);
-            Vec4<T>::store(dst + a.plane + o, oux);
-            Vec4<T>::store(dst + 2 * a.plane + o, ouy);
+            T* dst = static_cast<T*>(a.dst) + it.out + (size_t)(k - 2 * R - 2) * a.pitch;
+            Vec4<T>::store(dst, odr);
+            Vec4<T>::store(dst + a.plane, oux);
+            Vec4<T>::store(dst + 2 * a.plane, ouy);
         }
         // rotate the window: the oldest row/difference take the new ones
         if (R == 1) fm2 = nw;
@@ -286,6 +285,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
         it.first = min(kLoadCols, a.nx - it.x0);
         it.lane_stores = lane >= 1 && lane <= 30 && (it.strip0 - 4 + 4 * lane) < a.nx;
         it.base = base;
+        it.out = (size_t)it.yb * a.pitch + (it.strip0 - 4 + 4 * lane);
         // every lane is done with the slots of the previous item
         __syncwarp();
         // prologue: the first kSlots rows, two per issue

@@ -46,8 +46,12 @@ struct Vec4<float> {
         v[0] = make_float2(q.x, q.y);
         v[1] = make_float2(q.z, q.w);
     }
+    // two 8-byte stores straight from the column-pair registers (a 16-byte
+    // store would need both pairs in one aligned register quad); the halves
+    // of each 16-byte chunk merge in L2
     static __device__ __forceinline__ void store(float* p, const float2 v[2]) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float2*>(p)[0] = v[0];
+        reinterpret_cast<float2*>(p)[1] = v[1];
     }
 };
 template <>

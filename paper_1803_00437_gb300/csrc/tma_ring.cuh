@@ -64,8 +64,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+// Non-blocking test of a phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the given phase of a barrier; false if the spin bound ran out.
+// The common case (data already landed) costs one non-blocking test.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+    if (mbar_test_wait(bar, phase)) return true;
     for (uint32_t i = 0; i < kSpinLimit; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     return false;
