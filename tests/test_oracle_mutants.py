@@ -1,0 +1,121 @@
+"""The oracle's pins would catch a plausible mistake: each test plants one
+mistake in a copy of the oracle's source (on the CPU), builds it, and checks
+that at least one pin (Table 1 via the Jacobian, the closed-form shear
+wave, conservation, the Poiseuille curvature, the mean-flow viscosity)
+rejects the mutant while the unmodified oracle passes them all."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import linear
+from paper_1803_00437_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fdlbm_ref.c")
+
+MUTANTS = {
+    # sign of the strain-rate term of theta_XY (the paper's misprint)
+    "theta_xy_sign": ("(1.0 / 3.0) * (dx_Jy + dy_Jx)", "(1.0 / 3.0) * (dx_Jy - dy_Jx)"),
+    # a Jx row of M without its minus signs (as printed)
+    "m_row_sign": ("    {0, 1, 0, -1, 0, 1, -1, -1, 1},", "    {0, 1, 0, 1, 0, 1, 1, -1, 1},"),
+    # five-point weight 3/4 -> 2/3
+    "fd5_weight": ("return 0.75 * (FQ(i + di, j + dj)", "return (2.0 / 3.0) * (FQ(i + di, j + dj)"),
+    # propagation in the wrong direction in the FD-LBM step
+    "stream_direction": ("                    const int si = wrap(i - CX[a], nx);\n                    int sj = j - CY[a];\n                    if (!walls) sj = wrap(sj, ny);\n                    f[a] = fstar",
+                         "                    const int si = wrap(i + CX[a], nx);\n                    int sj = j + CY[a];\n                    if (!walls) sj = wrap(sj, ny);\n                    f[a] = fstar"),
+    # second half of the force dropped
+    "half_force": ("m[1] = Jx + 0.5 * p->force_x;", "m[1] = Jx;"),
+}
+
+
+def _build(tmp, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    d = tmp / name
+    d.mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "fdlbm_ref.h"), d)
+    (d / "fdlbm_ref.c").write_text(src.replace(old, new, 1))
+    lib = d / "lib.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    "-o", str(lib), str(d / "fdlbm_ref.c"), "-lm"], check=True)
+    return str(lib)
+
+
+def _pins_pass(ref):
+    """The pins, evaluated with the oracle module `ref` (its library path set)."""
+    failures = []
+    # 1. Jacobian of the step == symbol H(k) (pinned by Table 1), FD-5, 6x5 grid
+    p = ref.params(6, 5, 5, 1.7, 1.4)
+    X, Y = np.meshgrid(np.arange(6), np.arange(5))
+    h = 1e-6
+    for (m, n) in ((1, 0), (1, 2), (2, 1)):
+        kx, ky = 2 * np.pi * m / 6, 2 * np.pi * n / 5
+        ph = np.exp(1j * (kx * X + ky * Y))
+        B = np.zeros((3, 3), complex)
+        for c in range(3):
+            cols = []
+            for part in (ph.real, ph.imag):
+                o = []
+                for sg in (1, -1):
+                    st = [np.ones((5, 6)), np.zeros((5, 6)), np.zeros((5, 6))]
+                    st[c] = st[c] + sg * h * part
+                    o.append(np.array(ref.fd_run(p, *st, 1)))
+                cols.append((o[0] - o[1]) / (2 * h))
+            r = cols[0] + 1j * cols[1]
+            B[:, c] = (r * np.conj(ph)).mean(axis=(1, 2))
+        if np.abs(B - linear.H_fd(5, kx, ky, 1.7, 1.4)).max() > 1e-8:
+            failures.append("jacobian")
+            break
+    # 2. closed-form shear wave, three points
+    N, A, s = 32, 0.01, 1 / (3 * 0.02 + 0.5)
+    d, ux, uy = inputs.shear_wave(N, N, A, m=0, n=1, phase=np.pi / 2)
+    k = 2 * np.pi / N
+    r, x, yv = ref.fd_run(ref.params(N, N, 3, s, 1.5), 1 + d, ux, uy, 100)
+    z = 1 - (1 - np.cos(k)) / 3 + (1 - 1 / s) / 3 * np.sin(k) ** 2
+    yy = np.arange(N)[:, None] * np.ones((1, N))
+    if np.abs(x - A * z ** 100 * np.sin(k * yy)).max() > 1e-12 * A:
+        failures.append("shear")
+    # 3. Poiseuille curvature F / (2 nu), five points
+    nu, N = 0.1, 16
+    F = 8 * nu * 0.05 / (N ** 2)
+    pc = ref.params(4, N, 5, 1 / (3 * nu + 0.5), 1.5, boundary=1, wall_xi=0.5, force=(F, 0.0))
+    zf = np.zeros((N, 4))
+    r, x, yv = ref.fd_run(pc, 1 + zf, zf, zf, 4000)
+    u = x[:, 0]
+    yy = np.arange(N)
+    curv = -np.polyfit(yy[4:12], u[4:12], 2)[0]
+    if abs(curv / (F / (2 * nu)) - 1) > 2e-5:
+        failures.append("poiseuille")
+    return failures
+
+
+@pytest.fixture()
+def oracle_at(tmp_path):
+    from oracle import ref
+
+    def load(path):
+        ref._lib = None
+        ref.LIB = path
+        return ref
+
+    yield load
+    ref._lib = None
+    ref.LIB = os.path.join(ROOT, "oracle", "libfdlbm_ref.so")
+
+
+def test_unmodified_oracle_passes_the_pins(oracle_at):
+    from oracle import ref
+    ref.build()
+    assert _pins_pass(oracle_at(os.path.join(ROOT, "oracle", "libfdlbm_ref.so"))) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, oracle_at, name):
+    old, new = MUTANTS[name]
+    lib = _build(tmp_path, name, old, new)
+    failures = _pins_pass(oracle_at(lib))
+    assert failures, f"mutant {name} passed every pin"
