@@ -12,8 +12,9 @@ changes it by only ~nu k^2 ~ 1e-4 of its value.
   FP32 (2^-24): 1e-5 of A, the FP32 target.
   FP16 (2^-11 spacing): the stored value moves by less than a spacing per
        step, so errors accumulate like a random walk of half-spacings:
-       ~ sqrt(n) 2^-12 |u| ~ 8e-3 |u| after 1000 steps; bound 5e-3 of the
-       field amplitude pointwise and 1 % on decay rates.
+       ~ sqrt(n) 2^-12 |u| ~ 8e-3 |u| after 1000 steps; bound 1e-2 of the
+       field amplitude pointwise (that walk's scale, rounded up) and 1 % on
+       decay rates.
   BF16 (2^-8 spacing): the per-step change is below half a spacing, so the
        decay is rounded away; the storage cannot hold this state and is only
        checked to stay finite and bounded (recorded, not a target)."""
@@ -30,7 +31,7 @@ pytestmark = pytest.mark.gpu
 
 N, STEPS, AMP = 512, 1000, 1e-3
 # (max error / A, max error / field amplitude, decay-rate error)
-BOUNDS = {"f32": (1e-5, None, 1e-5), "f16": (None, 5e-3, 1e-2), "bf16": (None, 0.5, None)}
+BOUNDS = {"f32": (1e-5, None, 1e-5), "f16": (None, 1e-2, 1e-2), "bf16": (None, 0.5, None)}
 
 
 @pytest.fixture(scope="module")
