@@ -227,7 +227,7 @@ struct BatchRowStep {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
-                                dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
+                                pxx[h], cen.v[W_PXY][h], cen.v[W_PYY][h], dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
                                 dy.v[W_JY][h], dxpxx[h], dxpxy[h], dy.v[W_PXY][h],
                                 dy.v[W_PYY][h], kc, g[h]);
         const float in1 = __shfl_up_sync(kFull, g[1][1].y, 1);
@@ -576,10 +576,8 @@ static void fill_coeffs(const fdlbm_params& p, int R, StreamCoeffs* k) {
     k->e6 = (float)(6.0 * ae);
     k->e2 = (float)(2.0 * ae);
     k->em2 = (float)(-2.0 * ae);
-    k->x23 = (float)(2.0 / 3.0 * axx);
-    k->xm2 = (float)(-2.0 * axx);
+    k->xm23 = (float)(-2.0 / 3.0 * axx);
     k->x13 = (float)(axx / 3.0);
-    k->xm1 = (float)(-axx);
     k->hfx = (float)(0.5 * p.force_x);
     k->hfy = (float)(0.5 * p.force_y);
 }

@@ -107,22 +107,32 @@ __device__ __forceinline__ void issue_rows(const StreamArgs& a, const Ring<T>& r
     }
 }
 
+// Rows before this one are the window's warm-up: the centre row does not
+// exist yet (k < R) or the closed row is above the segment (k < 2R + 2).
+template <int R>
+__host__ __device__ constexpr int warm_rows() {
+    return 2 * R + 2;
+}
+
+// Wait (bounded) for field row k of the item to land in its slot.
+template <typename T>
+__device__ __forceinline__ bool row_landed(const Ring<T>& ring, const Item& it, int k) {
+    const uint32_t pos = it.base + k;
+    return mbar_wait_bounded(&ring.bars[pos & kSlotMask], (pos / kSlots) & 1u);
+}
+
 template <int R, bool FORCE, typename T>
 struct RowStep {
-    // Field row k of the item: wait for it, read it, update the y window and
-    // reconstruct the centre row c = row k - R; close and store row c - 1.
+    // Field row k of the item (already landed): read it, update the y window
+    // and reconstruct the centre row c = row k - R; close and store row c - 1.
+    // WARM: k may be below warm_rows<R>(), so the centre-row read and the
+    // store are guarded; otherwise both are unconditional.
+    template <bool WARM>
     static __device__ __forceinline__ void run(const StreamArgs& a, const Ring<T>& ring,
                                                const Item& it, int lane, int k, Win& fm2,
-                                               Win& fm1, Win& dm3, Win& dm2, Acc& acc,
-                                               bool& ok) {
+                                               Win& fm1, Win& dm3, Win& dm2, Acc& acc) {
         const uint32_t pos = it.base + k;
         const int slot = pos & kSlotMask;
-        const bool landed =
-            __all_sync(kFull, mbar_wait_bounded(&ring.bars[slot], (pos / kSlots) & 1u));
-        if (!landed) {
-            ok = false;
-            return;
-        }
         const int col = 4 + 4 * lane;  // slot column of this lane's first column
         float2 nr[2], nux[2], nuy[2];
         Vec4<T>::load(slot_field(ring, slot, 0) + col, nr);
@@ -143,7 +153,7 @@ struct RowStep {
         const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
-        if (k >= R) {
+        if (!WARM || k >= R) {
             if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
             Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
             Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
@@ -167,7 +177,8 @@ struct RowStep {
         // y derivatives at the centre row (scaled by 2 or 8):
         //   three points: 2 d/dy = f(c+1) - f(c-1)
         //   five points:  8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), d1(c+1) = f(r) - f(c);
-        //   the window holds n1 = -d1, so 8 d/dy = -6 n1(c) + n1(c-1) + n1(c+1)
+        //   the window holds n1 = -d1, so 8 d/dy = (-6 n1(c) + n1(c-1)) + n1(c+1);
+        //   the bracket does not wait for the new row
         Win dy, d1new;
 #pragma unroll
         for (int f = 0; f < W_N; ++f)
@@ -177,7 +188,7 @@ struct RowStep {
                     dy.v[f][h] = sub2(nw.v[f][h], fm2.v[f][h]);
                 } else {
                     d1new.v[f][h] = sub2(cen.v[f][h], nw.v[f][h]);
-                    dy.v[f][h] = fma2(sp(-6.f), dm2.v[f][h], add2(dm3.v[f][h], d1new.v[f][h]));
+                    dy.v[f][h] = add2(fma2(sp(-6.f), dm2.v[f][h], dm3.v[f][h]), d1new.v[f][h]);
                 }
             }
         // x derivatives at the centre row
@@ -194,7 +205,7 @@ struct RowStep {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
-                                dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
+                                pxx[h], cen.v[W_PXY][h], cen.v[W_PYY][h], dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
                                 dy.v[W_JY][h], dxpxx[h], dxpxy[h], dy.v[W_PXY][h],
                                 dy.v[W_PYY][h], a.k, g[h]);
 
@@ -241,7 +252,7 @@ struct RowStep {
             acc.ud[h] = du;
         }
         // destination row c - 1 = yb + k - 2R - 2 is an output row from k = 2R + 2
-        if (k >= 2 * R + 2 && it.lane_stores) {
+        if ((!WARM || k >= warm_rows<R>()) && it.lane_stores) {
             T* dst = static_cast<T*>(a.dst) + it.out + (size_t)(k - 2 * R - 2) * a.pitch;
             Vec4<T>::store(dst, odr);
             Vec4<T>::store(dst + a.plane, oux);
@@ -295,13 +306,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
         Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
         Acc acc = {};
         int k = 0;
+        using Step = RowStep<R, FORCE, T>;
         for (; k + 1 < it.nrows; k += 2) {
-            RowStep<R, FORCE, T>::run(a, ring, it, lane, k, w0, w1, w2, w3, acc, ok);
-            if (!ok) break;
-            RowStep<R, FORCE, T>::run(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc, ok);
-            if (!ok) {
-                ++k;
+            // one vote for both rows keeps their arithmetic in one block,
+            // free to interleave
+            const bool l0 = row_landed(ring, it, k), l1 = row_landed(ring, it, k + 1);
+            if (!__all_sync(kFull, l0 && l1)) {
+                ok = false;
                 break;
+            }
+            if (k >= warm_rows<R>()) {
+                Step::template run<false>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
+                Step::template run<false>(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc);
+            } else {
+                Step::template run<true>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
+                Step::template run<true>(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc);
             }
             // the centre rows of these two steps (k - R, k + 1 - R) are no
             // longer needed: refill their slots with the rows kSlots ahead
@@ -315,8 +334,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
             }
         }
         if (ok && k < it.nrows) {
-            RowStep<R, FORCE, T>::run(a, ring, it, lane, k, w0, w1, w2, w3, acc, ok);
-            if (ok) ++k;
+            if (__all_sync(kFull, row_landed(ring, it, k))) {
+                Step::template run<true>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
+                ++k;
+            } else {
+                ok = false;
+            }
         }
         consumed = base + k;
         base += it.nrows;
@@ -392,10 +415,8 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     a.k.e6 = (float)(6.0 * ae);
     a.k.e2 = (float)(2.0 * ae);
     a.k.em2 = (float)(-2.0 * ae);
-    a.k.x23 = (float)(2.0 / 3.0 * axx);
-    a.k.xm2 = (float)(-2.0 * axx);
+    a.k.xm23 = (float)(-2.0 / 3.0 * axx);
     a.k.x13 = (float)(axx / 3.0);
-    a.k.xm1 = (float)(-axx);
     a.k.hfx = (float)(0.5 * h->p.force_x);
     a.k.hfy = (float)(0.5 * h->p.force_y);
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);

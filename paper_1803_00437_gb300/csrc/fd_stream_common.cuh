@@ -96,8 +96,8 @@ struct Win {
 // Relaxation factors with the derivative scale (2 or 8) and the constants
 // of theta and of M^-1 folded in (see reconstruct2).
 struct StreamCoeffs {
-    float e6, e2, em2;         // theta_E terms, times (1 - 1/s_e) / (36 scale)
-    float x23, xm2, x13, xm1;  // theta_XX, theta_XY terms, times (1 - 1/s_xx) / scale
+    float e6, e2, em2;  // theta_E terms, times (1 - 1/s_e) / (36 scale)
+    float xm23, x13;    // -2/3 and 1/3, times (1 - 1/s_xx) / scale (theta_XX, theta_XY)
     float hfx, hfy;            // half of the body force
 };
 
@@ -129,32 +129,34 @@ __device__ __forceinline__ void deriv_x(const float2 v[2], float2 d[2]) {
 //   g1,3 = axis + XX/4 +- tx,  g2,4 = axis - XX/4 +- ty,
 //   g5,7 = diag + XY/4 +- (sx + sy),  g6,8 = diag - XY/4 +- (sy - sx),
 // with jx = Jx + F/2 (Strang) and q = -J, epsilon at equilibrium.
+// The equilibrium products rho ux ux = Pxx, rho ux uy = Pxy, rho uy uy = Pyy
+// are the window's momentum-flux values of the node.  The non-equilibrium
+// parts of theta_XX and theta_XY share E = grad rho + 3 (div P):
+//   K_XX = (2/3) a_xx [(dxJx - dyJy) - ux Ex + uy Ey]
+//   K_XY = (1/3) a_xx [(dxJy + dyJx) - ux Ey - uy Ex]
+// with Ex = dx rho + 3 (dx Pxx + dy Pxy), Ey = dy rho + 3 (dx Pxy + dy Pyy).
 template <bool FORCE>
 __device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, float2 Jx, float2 Jy,
-                                             float2 dxr, float2 dyr, float2 dxjx, float2 dyjx,
-                                             float2 dxjy, float2 dyjy, float2 dxpxx,
-                                             float2 dxpxy, float2 dypxy, float2 dypyy,
-                                             const StreamCoeffs& k, float2 g[9]) {
+                                             float2 pxx, float2 pxy, float2 pyy, float2 dxr,
+                                             float2 dyr, float2 dxjx, float2 dyjx, float2 dxjy,
+                                             float2 dyjy, float2 dxpxx, float2 dxpxy,
+                                             float2 dypxy, float2 dypyy, const StreamCoeffs& k,
+                                             float2 g[9]) {
     const float2 nuy = mul2(uy, sp(-1.f));
-    const float2 uxx = mul2(ux, ux), uyy = mul2(uy, uy), uxy = mul2(ux, uy);
-    const float2 u2 = add2(uxx, uyy);
-    const float2 mx = add2(dxpxx, dypxy);
-    const float2 my = add2(dxpxy, dypyy);
+    const float2 u2 = fma2(ux, ux, mul2(uy, uy));
+    const float2 ex = fma2(sp(3.f), add2(dxpxx, dypxy), dxr);
+    const float2 ey = fma2(sp(3.f), add2(dxpxy, dypyy), dyr);
     // K_E / 36 = a_e [(2 + 6 u^2)(d.J) - 2 (u . grad rho)] / 36
     const float2 udr = fma2(uy, dyr, mul2(ux, dxr));
     const float2 ke36 =
         fma2(sp(k.em2), udr, mul2(fma2(sp(k.e6), u2, sp(k.e2)), add2(dxjx, dyjy)));
-    // K_XX = a_xx [2/3 ((dxJx - dyJy) - (ux dxr - uy dyr)) - 2 (ux mx - uy my)]
-    const float2 b = sub2(sub2(dxjx, dyjy), fma2(ux, dxr, mul2(nuy, dyr)));
-    const float2 kxx = fma2(sp(k.x23), b, mul2(sp(k.xm2), fma2(ux, mx, mul2(nuy, my))));
-    // K_XY = a_xx [1/3 ((dxJy + dyJx) - (ux dyr + uy dxr)) - (ux my + uy mx)]
-    const float2 c = sub2(add2(dxjy, dyjx), fma2(ux, dyr, mul2(uy, dxr)));
-    const float2 kxy = fma2(sp(k.x13), c, mul2(sp(k.xm1), fma2(ux, my, mul2(uy, mx))));
-    // equilibrium parts: rho u2, rho (ux^2 - uy^2), rho ux uy
-    const float2 ru2_12 = mul2(fma2(dr, u2, u2), sp(1.f / 12.f));
-    const float2 dxx = sub2(uxx, uyy);
-    const float2 xx = add2(fma2(dr, dxx, dxx), kxx);
-    const float2 xy = add2(fma2(dr, uxy, uxy), kxy);
+    // K_XX = -(2/3) a_xx [ux Ex - uy Ey - (dxJx - dyJy)]
+    const float2 kxx = mul2(sp(k.xm23), fma2(ux, ex, fma2(nuy, ey, sub2(dyjy, dxjx))));
+    // K_XY = (1/3) a_xx [(dxJy + dyJx) - (ux Ey + uy Ex)]
+    const float2 kxy = mul2(sp(k.x13), sub2(add2(dxjy, dyjx), fma2(ux, ey, mul2(uy, ex))));
+    const float2 ru2_12 = mul2(add2(pxx, pyy), sp(1.f / 12.f));
+    const float2 xx = add2(sub2(pxx, pyy), kxx);
+    const float2 xy = add2(pxy, kxy);
     const float2 axis = sub2(fma2(dr, sp(1.f / 9.f), ru2_12), ke36);
     const float2 diag = fma2(sp(2.f), ke36, fma2(dr, sp(1.f / 36.f), ru2_12));
     g[0] = fma2(sp(-4.f), add2(axis, diag), dr);
