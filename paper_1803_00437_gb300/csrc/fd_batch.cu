@@ -34,7 +34,8 @@ namespace batch {
 
 using namespace stream;
 
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = 1;  // one-warp CTAs, 16 resident per SM (128 registers)
+constexpr int kMinBlocks = 16;
 constexpr int kStrip = 120;
 constexpr int kLoadCols = 136;
 constexpr int kSlots = 8;
@@ -139,20 +140,28 @@ __device__ __forceinline__ float row_factor(const Item& it, int r) {
     return f;
 }
 
+// Rows before this one are the window's warm-up (no centre row yet, or the
+// closed row is above the segment).
+template <int R>
+__host__ __device__ constexpr int warm_rows() {
+    return 2 * R + 2;
+}
+
+__device__ __forceinline__ bool row_landed(const Ring& ring, const Item& it, int k) {
+    const uint32_t pos = it.base + k;
+    return mbar_wait_bounded(&ring.bars[pos & kSlotMask], (pos / kSlots) & 1u);
+}
+
 template <int R, bool FORCE>
 struct BatchRowStep {
+    // Row k (already landed); WARM: k may be below warm_rows<R>().
+    template <bool WARM>
     static __device__ __forceinline__ void run(const Ring& ring, const Item& it,
                                                const StreamCoeffs& kc, int lane, int k,
-                                               Win& fm2, Win& fm1, Win& dm3, Win& dm2, Acc& acc,
-                                               bool& ok) {
+                                               Win& fm2, Win& fm1, Win& dm3, Win& dm2,
+                                               Acc& acc) {
         const uint32_t pos = it.base + k;
         const int slot = pos & kSlotMask;
-        const bool landed =
-            __all_sync(kFull, mbar_wait_bounded(&ring.bars[slot], (pos / kSlots) & 1u));
-        if (!landed) {
-            ok = false;
-            return;
-        }
         const int col = 4 + 4 * lane;
         float2 nr[2], nux[2], nuy[2];
         Vec4<float>::load(slot_field(ring, slot, 0) + col, nr);
@@ -178,7 +187,7 @@ struct BatchRowStep {
         const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
-        if (k >= R) {
+        if (!WARM || k >= R) {
             if (R == 2) Vec4<float>::load(slot_field(ring, cslot, 0) + col, cdr);
             Vec4<float>::load(slot_field(ring, cslot, 1) + col, cux);
             Vec4<float>::load(slot_field(ring, cslot, 2) + col, cuy);
@@ -212,7 +221,7 @@ struct BatchRowStep {
                     dy.v[f][h] = sub2(nw.v[f][h], fm2.v[f][h]);
                 } else {
                     d1new.v[f][h] = sub2(cen.v[f][h], nw.v[f][h]);
-                    dy.v[f][h] = fma2(sp(-6.f), dm2.v[f][h], add2(dm3.v[f][h], d1new.v[f][h]));
+                    dy.v[f][h] = add2(fma2(sp(-6.f), dm2.v[f][h], dm3.v[f][h]), d1new.v[f][h]);
                 }
             }
         float2 pxx[2], dxr[2], dxjx[2], dxjy[2], dxpxx[2], dxpxy[2];
@@ -266,7 +275,7 @@ struct BatchRowStep {
             acc.us[h] = su;
             acc.ud[h] = du;
         }
-        if (k >= 2 * R + 2 && it.lane_stores) {
+        if ((!WARM || k >= warm_rows<R>()) && it.lane_stores) {
             const int c0 = it.strip0 - 4 + 4 * lane;  // logical column of this lane
             const size_t row = (size_t)(it.yb + k - 2 * R - 2) * it.pitch;
             float* d0 = it.dst + row;
@@ -301,7 +310,7 @@ struct BatchRowStep {
 };
 
 template <int R, bool FORCE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) fd_batch_kernel(Args a) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kMinBlocks) fd_batch_kernel(Args a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp_bytes = kSlots * 3 * kLoadCols * (int)sizeof(float);
@@ -349,13 +358,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) fd_batch_kernel(Args a
         Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
         Acc acc = {};
         int k = 0;
+        using Step = BatchRowStep<R, FORCE>;
         for (; k + 1 < it.nrows; k += 2) {
-            BatchRowStep<R, FORCE>::run(ring, it, kc, lane, k, w0, w1, w2, w3, acc, ok);
-            if (!ok) break;
-            BatchRowStep<R, FORCE>::run(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc, ok);
-            if (!ok) {
-                ++k;
+            const bool l0 = row_landed(ring, it, k), l1 = row_landed(ring, it, k + 1);
+            if (!__all_sync(kFull, l0 && l1)) {
+                ok = false;
                 break;
+            }
+            if (k >= warm_rows<R>()) {
+                Step::template run<false>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+                Step::template run<false>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
+            } else {
+                Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+                Step::template run<true>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
             }
             __syncwarp();
             const int m1 = k + 1 - R;
@@ -367,8 +382,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) fd_batch_kernel(Args a
             }
         }
         if (ok && k < it.nrows) {
-            BatchRowStep<R, FORCE>::run(ring, it, kc, lane, k, w0, w1, w2, w3, acc, ok);
-            if (ok) ++k;
+            if (__all_sync(kFull, row_landed(ring, it, k))) {
+                Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+                ++k;
+            } else {
+                ok = false;
+            }
         }
         consumed = base + k;
         base += it.nrows;
@@ -662,6 +681,9 @@ static cudaError_t prepare_kernel(fdlbm_batch_t* b) {
     const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(float) + kSlots * 8);
     cudaError_t e = cudaFuncSetAttribute(fd_batch_kernel<R, FORCE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fd_batch_kernel<R, FORCE>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     if (b->grid == 0) {
         int sms = 0, per_sm = 0;
