@@ -109,6 +109,58 @@ def test_poiseuille_channel_256x64(oracle, scheme):
         assert np.abs(g - r[:, :1]).max() <= tol * umax
 
 
+def _parabola_walls(u, ny):
+    """Least-squares parabola through the channel profile u(y), y = 0..ny-1;
+    returns its roots (the measured wall positions) and its maximum."""
+    y = np.arange(ny, dtype=np.float64)
+    c2, c1, c0 = np.polyfit(y, u, 2)
+    r = np.sort(np.roots([c2, c1, c0]).real)
+    return r[0], r[1], c0 - c1 * c1 / (4 * c2)
+
+
+@pytest.mark.parametrize("scheme", ["fd5", "mrt"])
+def test_poiseuille_steady_state_256x64(oracle, scheme):
+    """Poiseuille channel 256 x 64 (walls at xi = 1/2, nu = 1/sqrt(108), force
+    for u_max = 0.05) run to steady state: 1e5 steps = 23 viscous times
+    H^2 / (pi^2 nu), so the slowest transient is below 1e-10 of u_max.
+
+    Tolerance: at the fixed point the same values repeat every step, so the
+    FP32 rounding of one step does not average out; it shifts the fixed point
+    by (rounding per step) x T, T = H^2 / (pi^2 nu) = 4300 steps the slowest
+    relaxation time.  One step rounds u's path about 8 times at ~|u|
+    (the sums of the six populations with c_x != 0, the close to u, the
+    force), so the bound is 8 eps T u_max, eps = 6e-8: 2e-3 of u_max.
+
+    Checks: the GPU profile equals the oracle's (4 columns of the same
+    channel) within that bound; the measured wall positions (roots of a
+    parabola fitted to u(y)) agree with the oracle's to the displacement it
+    allows (bound / |u'(wall)|, u'(wall) = 4 u_max / H); the walls sit within
+    0.1 of y = -xi and ny - 1 + xi (the closure's gate, Sec. 3-c); u_max is
+    within 2 % of F H^2 / (8 nu), H = ny - 1 + 2 xi."""
+    nu, ny, xi, steps = 1 / np.sqrt(108), 64, 0.5, 100000
+    H = ny - 1 + 2 * xi
+    F = 8 * nu * 0.05 / 64 ** 2
+    cfg = _cfg(256, ny, scheme, s_xx=_nu(nu), s_e=1.5, boundary="walls_y", wall_xi=xi,
+               force=(F, 0.0))
+    gpu, _ = gpu_run(cfg, as_f32(inputs.channel_at_rest(256, ny)), steps)
+    cfg4 = _cfg(4, ny, scheme, s_xx=_nu(nu), s_e=1.5, boundary="walls_y", wall_xi=xi,
+                force=(F, 0.0))
+    ref = oracle_run(oracle, cfg4, as_f32(inputs.channel_at_rest(4, ny)), steps)
+    umax = float(np.abs(ref[1]).max())
+    tol = 8 * 6e-8 * ny * ny / (np.pi ** 2 * nu)
+    errs = [float(np.abs(g - r[:, :1]).max()) / umax for g, r in zip(gpu, ref)]
+    print(f"{scheme}: steady-state max error / u_max {max(errs):.3e} (bound {tol:.3e})")
+    assert max(errs) <= tol
+    tol_y = tol * H / 4
+    y1g, y2g, umg = _parabola_walls(gpu[1][:, 0], ny)
+    y1r, y2r, umr = _parabola_walls(ref[1][:, 0], ny)
+    print(f"{scheme}: xi_m {-y1g:.5f} / {y2g - (ny - 1):.5f} (oracle {-y1r:.5f}), "
+          f"u_max {umg:.6f} (oracle {umr:.6f}, F H^2/8nu {F * H * H / (8 * nu):.6f})")
+    assert abs(y1g - y1r) <= tol_y and abs(y2g - y2r) <= tol_y
+    assert abs(y1g + xi) <= 0.1 and abs(y2g - (ny - 1 + xi)) <= 0.1
+    assert abs(umg / (F * H * H / (8 * nu)) - 1) <= 0.02
+
+
 def test_zero_steps_returns_initial_state(oracle):
     f = as_f32(inputs.random_fields(24, 20, 0.02, seed=1, rho_amp=0.01))
     for scheme in ("fd3", "fd5"):
