@@ -220,20 +220,41 @@ struct RowStep {
         const float in3 = __shfl_down_sync(kFull, g[0][3].x, 1);
         const float in6 = __shfl_down_sync(kFull, g[0][6].x, 1);
         const float in7 = __shfl_down_sync(kFull, g[0][7].x, 1);
-        // per destination column j: from j - 1 (1, 5, 8) and from j + 1 (3, 6, 7)
-        const float2 p1[2] = {make_float2(in1, g[0][1].x), make_float2(g[0][1].y, g[1][1].x)};
-        const float2 p5[2] = {make_float2(in5, g[0][5].x), make_float2(g[0][5].y, g[1][5].x)};
-        const float2 p8[2] = {make_float2(in8, g[0][8].x), make_float2(g[0][8].y, g[1][8].x)};
-        const float2 p3[2] = {make_float2(g[0][3].y, g[1][3].x), make_float2(g[1][3].y, in3)};
-        const float2 p6[2] = {make_float2(g[0][6].y, g[1][6].x), make_float2(g[1][6].y, in6)};
-        const float2 p7[2] = {make_float2(g[0][7].y, g[1][7].x), make_float2(g[1][7].y, in7)};
+        // per destination column j (0..3): from j - 1 (1, 5, 8) and j + 1
+        // (3, 6, 7), summed in scalar FP32 (the results land in column pairs
+        // without register moves)
+        float G[9][4];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            G[q][0] = g[0][q].x;
+            G[q][1] = g[0][q].y;
+            G[q][2] = g[1][q].x;
+            G[q][3] = g[1][q].y;
+        }
+        float ss_[4], ds_[4], su_[4], du_[4], sd_[4], dd_[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float q1 = j ? G[1][j - 1] : in1, q5 = j ? G[5][j - 1] : in5;
+            const float q8 = j ? G[8][j - 1] : in8;
+            const float q3 = j < 3 ? G[3][j + 1] : in3, q6 = j < 3 ? G[6][j + 1] : in6;
+            const float q7 = j < 3 ? G[7][j + 1] : in7;
+            ss_[j] = G[0][j] + (q1 + q3);
+            ds_[j] = q1 - q3;
+            su_[j] = G[2][j] + (q5 + q6);
+            du_[j] = q5 - q6;
+            sd_[j] = G[4][j] + (q7 + q8);
+            dd_[j] = q8 - q7;
+        }
 
         float2 odr[2], oux[2], ouy[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float2 ss = add2(g[h][0], add2(p1[h], p3[h])), ds = sub2(p1[h], p3[h]);
-            const float2 su = add2(g[h][2], add2(p5[h], p6[h])), du = sub2(p5[h], p6[h]);
-            const float2 sd = add2(g[h][4], add2(p7[h], p8[h])), dd = sub2(p8[h], p7[h]);
+            const float2 ss = make_float2(ss_[2 * h], ss_[2 * h + 1]);
+            const float2 ds = make_float2(ds_[2 * h], ds_[2 * h + 1]);
+            const float2 su = make_float2(su_[2 * h], su_[2 * h + 1]);
+            const float2 du = make_float2(du_[2 * h], du_[2 * h + 1]);
+            const float2 sd = make_float2(sd_[2 * h], sd_[2 * h + 1]);
+            const float2 dd = make_float2(dd_[2 * h], dd_[2 * h + 1]);
             // close row c - 1: u = J - J dr / (1 + dr)
             const float2 drn = add2(acc.ar[h], sd);
             float2 px = add2(acc.ax[h], dd);

@@ -21,11 +21,13 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
 }
 
-// Hardware reciprocal (relative error ~2^-23).  Used only where it scales a
+// Hardware reciprocal (relative error ~2^-23), flushing subnormals (its
+// argument is -(1 + rho') ~ -1, never subnormal; the non-flushing form adds
+// subnormal handling around the reciprocal).  Used only where it scales a
 // small correction term, so its error is far below FP32 resolution.
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
-    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
