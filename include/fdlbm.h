@@ -109,7 +109,9 @@ size_t fdlbm_workspace_size(const fdlbm_params* params);
 int fdlbm_create(const fdlbm_params* params, void* workspace, size_t workspace_bytes,
                  void* stream, fdlbm_t** out);
 
-/* Release the host-side handle.  Never touches the workspace. */
+/* Release the host-side handle (and its 48-byte page-locked landing area for
+ * reduction results, allocated by fdlbm_create).  Never touches the
+ * workspace. */
 void fdlbm_destroy(fdlbm_t* h);
 
 /* Change the stream that later calls are enqueued on. */
@@ -120,8 +122,11 @@ int fdlbm_set_stream(fdlbm_t* h, void* stream);
  * Sec. 1-a at (rho, J = rho u - F/2), so the reported velocity is u. */
 int fdlbm_init(fdlbm_t* h, const float* drho, const float* ux, const float* uy);
 
-/* Same, from host arrays (copied through the workspace staging area; waits
- * for the copies to finish before returning). */
+/* Same, from host arrays; waits until the state is initialised.  Arrays in
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister, e.g. torch's
+ * pin_memory) are read in place by the init kernel over the host link;
+ * other host arrays are copied through the workspace staging area first.
+ * The arrays are only read, and may be reused once the call returns. */
 int fdlbm_init_host(fdlbm_t* h, const float* drho, const float* ux, const float* uy);
 
 /* Initial state rho = 1 and u = V + sum of transverse plane waves
@@ -259,6 +264,17 @@ int fdlbm_sync(fdlbm_t* h);
 
 /* Text of the last error on this handle ("" if none); valid until the next
  * call on the handle.  fdlbm_status_string maps a status code to its name. */
+/* Failure-detection self test (the paper has no counterpart): enqueue one
+ * warp that waits on a device barrier nothing will complete, bounded by
+ * `tries` polls (a poll may suspend the warp for a hardware-defined slice;
+ * 1000 polls take well under a second).  On expiry it records
+ * FDLBM_ERR_TIMEOUT in the handle's status word, as a step kernel does when
+ * a bulk copy does not land in time, and returns; the next fdlbm_sync or
+ * fdlbm_reduce returns FDLBM_ERR_TIMEOUT and clears the word.  Nothing is in
+ * flight when the warp gives up, so the device stays usable.  Returns
+ * FDLBM_OK once enqueued, FDLBM_ERR_INVALID for tries < 0. */
+int fdlbm_selftest_wait_timeout(fdlbm_t* h, int32_t tries);
+
 const char* fdlbm_last_error(const fdlbm_t* h);
 const char* fdlbm_status_string(int status);
 

@@ -1,4 +1,6 @@
 // aux_kernels.cu -- initialisation, moment extraction and FP64 reductions.
+#include <algorithm>
+
 #include "mrt_common.cuh"
 
 namespace fdlbm {
@@ -18,6 +20,34 @@ __global__ void fd_init_kernel(const float* __restrict__ drho, const float* __re
     Storage<T>::store(dst + o, drho[i]);
     Storage<T>::store(dst + plane + o, ux[i]);
     Storage<T>::store(dst + 2 * plane + o, uy[i]);
+}
+
+// Four consecutive columns per thread (nx % 4 == 0, sources 16-byte
+// aligned): 16-byte loads, which is what keeps the host link busy when the
+// sources are page-locked host memory read in place.
+template <typename T>
+__device__ __forceinline__ void store4(T* p, float4 v) {
+    Storage<T>::store(p, v.x);
+    Storage<T>::store(p + 1, v.y);
+    Storage<T>::store(p + 2, v.z);
+    Storage<T>::store(p + 3, v.w);
+}
+template <>
+__device__ __forceinline__ void store4<float>(float* p, float4 v) {
+    *reinterpret_cast<float4*>(p) = v;  // rows start 256-byte aligned
+}
+
+template <typename T>
+__global__ void fd_init_vec4_kernel(const float4* __restrict__ drho, const float4* __restrict__ ux,
+                                    const float4* __restrict__ uy, T* __restrict__ dst, int nx4,
+                                    int ny, size_t pitch, size_t plane) {
+    const int x4 = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+    if (x4 >= nx4) return;
+    const size_t i = (size_t)y * nx4 + x4, o = (size_t)y * pitch + 4 * (size_t)x4;
+    const float4 a = drho[i], b = ux[i], c = uy[i];
+    store4(dst + o, a);
+    store4(dst + plane + o, b);
+    store4(dst + 2 * plane + o, c);
 }
 
 // ---- MRT: equilibrium start --------------------------------------------------
@@ -151,67 +181,137 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// slot 3 counts non-finite nodes in every reduction
-template <typename T, int KIND>
+// Compensated FP32 sum (Knuth's TwoSum; no products, so nothing to contract
+// into FMAs): s + c carries ~48 significant bits.  The FP32 pipes of this GPU
+// are ~60x faster than its FP64 pipe, so the per-node work of the mass and
+// momentum sums stays in FP32 and only each thread's chunk total (<= 64
+// terms) is added in FP64.
+struct Sum2f {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (v - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double flush() {
+        const double r = (double)s + (double)c;
+        s = c = 0.f;
+        return r;
+    }
+};
+
+// rho u = u + dr u, with dr u split exactly into p + e (FMA product error).
+__device__ __forceinline__ void add_rho_u(Sum2f& acc, float dr, float u) {
+    const float p = dr * u;
+    const float e = fmaf(dr, u, -p);
+    acc.add(u);
+    acc.add(p);
+    acc.add(e);
+}
+
+// Rows per block iteration; for the mode projection their phases
+// e^{i ky y} are tabulated in shared memory once per block.
+constexpr int kRowChunk = 64;
+
+// One column per thread (x = column chunk of the block + thread), rows in
+// chunks strided over gridDim.y; slot 3 counts non-finite nodes in every
+// reduction.  The mode projection uses the separable phase
+// e^{i(kx x + ky y)} = e^{i kx x} e^{i ky y}: the column factor once per
+// thread and row chunk, the row factors from the shared table (FP64 sincos
+// of exact integer multiples, no accumulated rotation).
+template <typename T, int KIND, int WHAT>
 __global__ void __launch_bounds__(kThreads)
     reduce_kernel(const void* s, int nx, int ny, size_t pitch, size_t plane, float fx, float fy,
-                  int what, double a0, double a1, double* __restrict__ partial) {
+                  double a0, double a1, double* __restrict__ partial) {
     double acc[kReduceSlots] = {0.0, 0.0, 0.0, 0.0};
-    const int64_t total = (int64_t)nx * ny;
+    __shared__ double2 rowph[kRowChunk];
     double kx = 0.0, ky = 0.0, tx = 0.0, ty = 0.0;
-    if (what == FDLBM_REDUCE_MODE) {
+    if (WHAT == FDLBM_REDUCE_MODE) {
         kx = 2.0 * M_PI * a0 / nx;
         ky = 2.0 * M_PI * a1 / ny;
         const double kk = sqrt(kx * kx + ky * ky);
         tx = kk > 0.0 ? -ky / kk : 0.0;
         ty = kk > 0.0 ? kx / kk : 0.0;
     }
-    for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < total;
-         n += (int64_t)gridDim.x * kThreads) {
-        const int x = (int)(n % nx), y = (int)(n / nx);
-        float dr, ux, uy;
-        node_state<T, KIND>(s, x, y, nx, ny, pitch, plane, fx, fy, &dr, &ux, &uy);
-        if (!(isfinite(dr) && isfinite(ux) && isfinite(uy))) {
-            acc[3] += 1.0;
-            continue;
-        }
-        const double rho = 1.0 + (double)dr;
-        switch (what) {
-            case FDLBM_REDUCE_MASS: acc[0] += (double)dr; break;
-            case FDLBM_REDUCE_MOMENTUM:
-                acc[0] += rho * ux;
-                acc[1] += rho * uy;
-                break;
-            case FDLBM_REDUCE_ENERGY:
-                acc[0] += 0.5 * rho * ((double)ux * ux + (double)uy * uy);
-                break;
-            case FDLBM_REDUCE_MODE: {
-                const double ut = tx * ux + ty * uy;
+    for (int y0 = blockIdx.y * kRowChunk; y0 < ny; y0 += gridDim.y * kRowChunk) {
+        const int nrows = min(kRowChunk, ny - y0);
+        if (WHAT == FDLBM_REDUCE_MODE) {
+            __syncthreads();
+            if (threadIdx.x < nrows) {
                 double sn, cs;
-                sincos(kx * x + ky * y, &sn, &cs);
-                acc[0] += ut * cs;
-                acc[1] -= ut * sn;
-                break;
+                sincos(ky * (double)(y0 + (int)threadIdx.x), &sn, &cs);
+                rowph[threadIdx.x] = make_double2(cs, sn);
             }
-            default:
-                acc[0] = fmax(acc[0], sqrt((double)ux * ux + (double)uy * uy));
-                acc[1] = fmax(acc[1], fabs((double)dr));
+            __syncthreads();
+        }
+        for (int x = blockIdx.x * kThreads + threadIdx.x; x < nx; x += gridDim.x * kThreads) {
+            double cxc = 1.0, cxs = 0.0;
+            if (WHAT == FDLBM_REDUCE_MODE) sincos(kx * (double)x, &cxs, &cxc);
+            Sum2f f0, f1;
+            int bad = 0;
+            // rows in batches of kBatch: all loads of a batch are issued before
+            // any is used (several rows in flight per warp); a non-finite node
+            // is counted and contributes zero
+            constexpr int kBatch = 8;
+            for (int r0 = 0; r0 < nrows; r0 += kBatch) {
+                float bdr[kBatch], bux[kBatch], buy[kBatch];
+#pragma unroll
+                for (int i = 0; i < kBatch; ++i) {
+                    bdr[i] = bux[i] = buy[i] = 0.f;
+                    if (r0 + i < nrows)
+                        node_state<T, KIND>(s, x, y0 + r0 + i, nx, ny, pitch, plane, fx, fy,
+                                            &bdr[i], &bux[i], &buy[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < kBatch; ++i) {
+                    const bool ok = isfinite(bdr[i]) && isfinite(bux[i]) && isfinite(buy[i]);
+                    bad += ok ? 0 : 1;
+                    const float dr = ok ? bdr[i] : 0.f;
+                    const float ux = ok ? bux[i] : 0.f;
+                    const float uy = ok ? buy[i] : 0.f;
+                    const double rho = 1.0 + (double)dr;
+                    if (WHAT == FDLBM_REDUCE_MASS) {
+                        f0.add(dr);
+                    } else if (WHAT == FDLBM_REDUCE_MOMENTUM) {
+                        add_rho_u(f0, dr, ux);
+                        add_rho_u(f1, dr, uy);
+                    } else if (WHAT == FDLBM_REDUCE_ENERGY) {
+                        acc[0] += 0.5 * rho * ((double)ux * ux + (double)uy * uy);
+                    } else if (WHAT == FDLBM_REDUCE_MODE) {
+                        const double ut = tx * ux + ty * uy;
+                        const double2 ry = rowph[r0 + i];
+                        const double cs = cxc * ry.x - cxs * ry.y;  // cos(kx x + ky y)
+                        const double sn = cxs * ry.x + cxc * ry.y;  // sin(kx x + ky y)
+                        acc[0] += ut * cs;
+                        acc[1] -= ut * sn;
+                    } else {
+                        acc[0] = fmax(acc[0], sqrt((double)ux * ux + (double)uy * uy));
+                        acc[1] = fmax(acc[1], fabs((double)dr));
+                    }
+                }
+            }
+            acc[3] += (double)bad;
+            if (WHAT == FDLBM_REDUCE_MASS || WHAT == FDLBM_REDUCE_MOMENTUM) {
+                acc[0] += f0.flush();
+                acc[1] += f1.flush();
+            }
         }
     }
     __shared__ double sh[kThreads / 32][kReduceSlots];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool maxw = WHAT == FDLBM_REDUCE_MAXABS;
     for (int k = 0; k < kReduceSlots; ++k) {
-        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
-        const double v = is_max ? warp_max(acc[k]) : warp_sum(acc[k]);
+        const double v = (maxw && k < 2) ? warp_max(acc[k]) : warp_sum(acc[k]);
         if (lane == 0) sh[wid][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < kReduceSlots) {
         const int k = threadIdx.x;
-        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+        const bool is_max = maxw && k < 2;
         double v = sh[0][k];
         for (int w = 1; w < kThreads / 32; ++w) v = is_max ? fmax(v, sh[w][k]) : v + sh[w][k];
-        partial[blockIdx.x * kReduceSlots + k] = v;
+        partial[(blockIdx.y * gridDim.x + blockIdx.x) * kReduceSlots + k] = v;
     }
 }
 
@@ -245,6 +345,31 @@ cudaError_t dispatch_kind(fdlbm_s* h, F&& f) {
 
 cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
                            void* dst) {
+    const bool vec4 = h->p.nx % 4 == 0 &&
+                      ((reinterpret_cast<uintptr_t>(drho) | reinterpret_cast<uintptr_t>(ux) |
+                        reinterpret_cast<uintptr_t>(uy)) & 15) == 0;
+    if (vec4) {
+        const int nx4 = h->p.nx / 4;
+        dim3 grid4((nx4 + kThreads - 1) / kThreads, h->p.ny);
+        const float4* a = reinterpret_cast<const float4*>(drho);
+        const float4* b = reinterpret_cast<const float4*>(ux);
+        const float4* c = reinterpret_cast<const float4*>(uy);
+        switch (h->p.storage) {
+            case FDLBM_STORAGE_F16:
+                fd_init_vec4_kernel<__half><<<grid4, kThreads, 0, h->stream>>>(
+                    a, b, c, static_cast<__half*>(dst), nx4, h->p.ny, h->L.pitch, h->L.plane);
+                break;
+            case FDLBM_STORAGE_BF16:
+                fd_init_vec4_kernel<__nv_bfloat16><<<grid4, kThreads, 0, h->stream>>>(
+                    a, b, c, static_cast<__nv_bfloat16*>(dst), nx4, h->p.ny, h->L.pitch,
+                    h->L.plane);
+                break;
+            default:
+                fd_init_vec4_kernel<float><<<grid4, kThreads, 0, h->stream>>>(
+                    a, b, c, static_cast<float*>(dst), nx4, h->p.ny, h->L.pitch, h->L.plane);
+        }
+        return cudaGetLastError();
+    }
     dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
     switch (h->p.storage) {
         case FDLBM_STORAGE_F16:
@@ -304,18 +429,36 @@ struct MomentsLaunch {
     }
 };
 
+// Grid of the reduction: column chunks x row chunks, at most kReduceBlocks
+// blocks (the size of the partial-sum area).
+dim3 reduce_grid(int nx, int ny) {
+    const int gx = std::min((nx + kThreads - 1) / kThreads, kReduceBlocks);
+    const int gy = std::max(1, std::min((ny + kRowChunk - 1) / kRowChunk, kReduceBlocks / gx));
+    return dim3(gx, gy);
+}
+
 struct ReduceLaunch {
     fdlbm_s* h;
     const void* s;
     int what;
     double a0, a1;
     double* partial;
+    template <typename T, int KIND, int WHAT>
+    cudaError_t go() {
+        reduce_kernel<T, KIND, WHAT><<<reduce_grid(h->p.nx, h->p.ny), kThreads, 0, h->stream>>>(
+            s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
+            (float)h->p.force_y, a0, a1, partial);
+        return cudaGetLastError();
+    }
     template <typename T, int KIND>
     cudaError_t run() {
-        reduce_kernel<T, KIND><<<kReduceBlocks, kThreads, 0, h->stream>>>(
-            s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
-            (float)h->p.force_y, what, a0, a1, partial);
-        return cudaGetLastError();
+        switch (what) {
+            case FDLBM_REDUCE_MASS: return go<T, KIND, FDLBM_REDUCE_MASS>();
+            case FDLBM_REDUCE_MOMENTUM: return go<T, KIND, FDLBM_REDUCE_MOMENTUM>();
+            case FDLBM_REDUCE_ENERGY: return go<T, KIND, FDLBM_REDUCE_ENERGY>();
+            case FDLBM_REDUCE_MODE: return go<T, KIND, FDLBM_REDUCE_MODE>();
+            default: return go<T, KIND, FDLBM_REDUCE_MAXABS>();
+        }
     }
 };
 }  // namespace
@@ -330,7 +473,8 @@ cudaError_t launch_reduce(fdlbm_s* h, const void* state, int what, double a0, do
     ReduceLaunch rl{h, state, what, a0, a1, partial};
     cudaError_t e = dispatch_kind(h, rl);
     if (e != cudaSuccess) return e;
-    reduce_final_kernel<<<1, 32, 0, h->stream>>>(partial, kReduceBlocks, what, result);
+    const dim3 g = reduce_grid(h->p.nx, h->p.ny);
+    reduce_final_kernel<<<1, 32, 0, h->stream>>>(partial, (int)(g.x * g.y), what, result);
     return cudaGetLastError();
 }
 

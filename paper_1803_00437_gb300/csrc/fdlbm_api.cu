@@ -6,6 +6,31 @@
 #include <new>
 
 #include "fdlbm_internal.cuh"
+#include "tma_ring.cuh"
+
+namespace fdlbm {
+namespace {
+// Failure-detection self test: one warp waits on a barrier whose arrival
+// never comes, with a bound of `tries` polls, and reports the expiry through
+// the status word as the step kernels do.  No copy is in flight, so the
+// kernel ends cleanly after recording the error.
+__global__ void selftest_wait_kernel(int* status, uint32_t tries) {
+    __shared__ uint64_t bar;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const bool landed = __all_sync(0xffffffffu, mbar_wait_tries(&bar, 0, tries));
+    __syncwarp();
+    if (lane == 0) {
+        if (!landed) atomicExch(status, FDLBM_ERR_TIMEOUT);
+        mbar_inval(&bar);
+    }
+}
+}  // namespace
+}  // namespace fdlbm
 
 namespace fdlbm {
 
@@ -171,11 +196,20 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
         delete h;
         return FDLBM_ERR_CUDA;
     }
+    h->host_io = nullptr;
+    void* hio = nullptr;
+    if (cudaHostAlloc(&hio, sizeof(fdlbm_s::HostIO), cudaHostAllocDefault) == cudaSuccess)
+        h->host_io = static_cast<fdlbm_s::HostIO*>(hio);
+    else
+        cudaGetLastError();  // reductions then go through pageable memory
     *out = h;
     return FDLBM_OK;
 }
 
-void fdlbm_destroy(fdlbm_t* h) { delete h; }
+void fdlbm_destroy(fdlbm_t* h) {
+    if (h && h->host_io) cudaFreeHost(h->host_io);
+    delete h;
+}
 
 int fdlbm_set_stream(fdlbm_t* h, void* stream) {
     if (!h) return FDLBM_ERR_INVALID;
@@ -210,8 +244,30 @@ int fdlbm_init_host(fdlbm_t* h, const float* drho, const float* ux, const float*
     DeviceGuard g(h->device);
     if (!g.ok) return set_error(h, FDLBM_ERR_CUDA, "cannot select the handle's device");
     const size_t n = (size_t)h->p.nx * h->p.ny;
-    float* st = staging(h);
     const float* src[3] = {drho, ux, uy};
+    // Page-locked host arrays are device-addressable: the init kernel reads
+    // them in place over the host link (one pass, no staging copy).
+    const float* mapped[3] = {nullptr, nullptr, nullptr};
+    bool in_place = true;
+    for (int k = 0; k < 3 && in_place; ++k) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, src[k]) != cudaSuccess) {
+            cudaGetLastError();  // not a CUDA-known pointer: clear and stage
+            in_place = false;
+        } else if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr) {
+            mapped[k] = static_cast<const float*>(at.devicePointer);
+        } else {
+            in_place = false;
+        }
+    }
+    if (in_place) {
+        int rc = init_from_device(h, mapped[0], mapped[1], mapped[2]);
+        if (rc != FDLBM_OK) return rc;
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "init_host sync");
+        return FDLBM_OK;
+    }
+    float* st = staging(h);
     for (int k = 0; k < 3; ++k) {
         cudaError_t e = cudaMemcpyAsync(st + k * n, src[k], n * sizeof(float),
                                         cudaMemcpyHostToDevice, h->stream);
@@ -306,9 +362,17 @@ int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out) {
     cudaError_t e = launch_reduce(h, state_ptr(h, h->cur), what, a0, a1, partial, result);
     h->launches += 2;
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce kernel");
-    double host[kReduceSlots];
-    e = cudaMemcpyAsync(host, result, sizeof(host), cudaMemcpyDeviceToHost, h->stream);
+    double stack_host[kReduceSlots];
+    double* host = h->host_io ? h->host_io->result : stack_host;
+    e = cudaMemcpyAsync(host, result, sizeof(double) * kReduceSlots, cudaMemcpyDeviceToHost,
+                        h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce copy");
+    int* dflag = reinterpret_cast<int*>(h->ws + h->L.off_flag);
+    if (h->host_io) {  // the status word rides along: one synchronisation
+        e = cudaMemcpyAsync(&h->host_io->flag, dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                            h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    }
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce sync");
     const int nout = (what == FDLBM_REDUCE_MOMENTUM || what == FDLBM_REDUCE_MODE ||
@@ -319,7 +383,14 @@ int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out) {
     if (host[3] != 0.0)
         return set_error(h, FDLBM_ERR_DIVERGED, "reduce: %.0f nodes hold non-finite values",
                          host[3]);
-    return device_status(h);
+    if (!h->host_io) return device_status(h);
+    const int flag = h->host_io->flag;
+    if (flag != 0) {
+        cudaMemsetAsync(dflag, 0, sizeof(int), h->stream);
+        return set_error(h, flag, "device reported %s (a bounded wait expired)",
+                         flag == FDLBM_ERR_TIMEOUT ? "FDLBM_ERR_TIMEOUT" : "an error");
+    }
+    return FDLBM_OK;
 }
 
 int fdlbm_sync(fdlbm_t* h) {
@@ -328,6 +399,19 @@ int fdlbm_sync(fdlbm_t* h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sync");
     return device_status(h);
+}
+
+int fdlbm_selftest_wait_timeout(fdlbm_t* h, int32_t tries) {
+    if (!h) return FDLBM_ERR_INVALID;
+    if (tries < 0) return set_error(h, FDLBM_ERR_INVALID, "selftest: tries < 0");
+    DeviceGuard g(h->device);
+    if (!g.ok) return set_error(h, FDLBM_ERR_CUDA, "cannot select the handle's device");
+    int* dflag = reinterpret_cast<int*>(h->ws + h->L.off_flag);
+    fdlbm::selftest_wait_kernel<<<1, 32, 0, h->stream>>>(dflag, (uint32_t)tries);
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "selftest kernel");
+    return FDLBM_OK;
 }
 
 const char* fdlbm_last_error(const fdlbm_t* h) { return h ? h->err : "NULL handle"; }

@@ -86,7 +86,7 @@ struct Layout {
     size_t total;
 };
 
-constexpr int kReduceBlocks = 608;  // 4 x 152 SMs
+constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs (full occupancy at 256 threads)
 constexpr int kReduceSlots = 4;     // doubles per block partial
 
 bool compute_layout(const fdlbm_params& p, Layout* L);
@@ -103,6 +103,13 @@ struct fdlbm_s {
     int64_t launches;
     int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
     int fd_path;            // 0: automatic, 1: force the tiled FD kernel
+    // page-locked host landing area for reduction results and the device
+    // status word (one synchronisation per reduction); NULL if unavailable
+    struct HostIO {
+        double result[4];
+        int flag;
+        int pad;
+    }* host_io;
     char err[512];
 };
 

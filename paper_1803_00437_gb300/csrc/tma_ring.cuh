@@ -77,6 +77,15 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+// Wait for the given phase of a barrier with an explicit bound of `tries`
+// polls; false if it ran out.
+__device__ __forceinline__ bool mbar_wait_tries(uint64_t* bar, uint32_t phase, uint32_t tries) {
+    if (mbar_test_wait(bar, phase)) return true;
+    for (uint32_t i = 0; i < tries; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
 // Wait for the given phase of a barrier; false if the spin bound ran out.
 // The common case (data already landed) costs one non-blocking test.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {

@@ -85,6 +85,8 @@ def load_library(path: str | None = None):
         L.fdlbm_moments_host.argtypes = [vp, fp, fp, fp]
         L.fdlbm_reduce.argtypes = [vp, ctypes.c_int32, fp, fp]
         L.fdlbm_sync.argtypes = [vp]
+        L.fdlbm_selftest_wait_timeout.argtypes = [vp, ctypes.c_int32]
+        L.fdlbm_selftest_wait_timeout.restype = ctypes.c_int
         L.fdlbm_last_error.argtypes = [vp]
         L.fdlbm_last_error.restype = cp
         L.fdlbm_status_string.argtypes = [ctypes.c_int]
@@ -299,6 +301,12 @@ class Lattice:
 
     def sync(self):
         self._check(self.lib.fdlbm_sync(self._h), "sync")
+
+    def selftest_wait_timeout(self, tries: int = 1000):
+        """Enqueue the failure-detection self test (a bounded device wait that
+        runs out); the next sync() or reduce() raises FdlbmError with status
+        ERR_TIMEOUT."""
+        self._check(self.lib.fdlbm_selftest_wait_timeout(self._h, int(tries)), "selftest")
 
     @property
     def launches(self) -> int:

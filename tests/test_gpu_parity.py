@@ -286,6 +286,39 @@ def test_host_round_trip_and_errors():
     assert lat.launches > 0
 
 
+@pytest.mark.parametrize("scheme,storage,shape", [("fd5", "f32", (256, 40)),
+                                                  ("fd5", "f32", (50, 30)),
+                                                  ("fd5", "f16", (256, 40)),
+                                                  ("mrt", "f32", (64, 24))])
+def test_init_host_pinned_reads_in_place(scheme, storage, shape):
+    """fdlbm_init_host from page-locked host memory (read in place by the
+    init kernel; 16-byte loads when nx % 4 == 0) gives exactly the state of
+    fdlbm_init from device memory, before and after 5 steps."""
+    import ctypes
+    import torch
+    nx, ny = shape
+    f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=9, rho_amp=0.01))
+    cfg = _cfg(nx, ny, scheme, storage=storage)
+    a, _ = gpu_run(cfg, f, 0)
+    from paper_1803_00437_gb300 import fdlbm as F
+    lat = F.Lattice(cfg)
+    host = [torch.from_numpy(x).pin_memory() for x in f]
+    lat._check(lat.lib.fdlbm_init_host(lat._h, *[ctypes.c_void_p(t.data_ptr()) for t in host]),
+               "init_host")
+    for x in host:
+        x.fill_(float("nan"))  # the call has returned: the arrays are free again
+    got = [t.cpu().numpy().astype(np.float64) for t in lat.moments()]
+    lat.sync()
+    for g, r in zip(got, a):
+        assert np.array_equal(g, r)
+    lat.step(5)
+    b, _ = gpu_run(cfg, f, 5)
+    got = [t.cpu().numpy().astype(np.float64) for t in lat.moments()]
+    lat.sync()
+    for g, r in zip(got, b):
+        assert np.array_equal(g, r)
+
+
 @pytest.mark.parametrize("scheme", ["fd3", "fd5"])
 @pytest.mark.parametrize("shape", [(256, 64), (264, 40), (512, 37), (384, 100), (1024, 16)])
 def test_streaming_kernel_parity(oracle, scheme, shape):
