@@ -250,6 +250,11 @@ __global__ void __launch_bounds__(kThreads)
             if (WHAT == FDLBM_REDUCE_MODE) sincos(kx * (double)x, &cxs, &cxc);
             Sum2f f0, f1;
             int bad = 0;
+            // max |u|: FP32 |u|^2 (relative error < 2.4e-7) screens the nodes and
+            // only those within 1e-4 of the running FP32 maximum are squared in
+            // FP64, so the node holding the true maximum is always among them
+            float m32 = 0.f, dmax = 0.f;
+            double m64 = 0.0;
             // rows in batches of kBatch: all loads of a batch are issued before
             // any is used (several rows in flight per warp); a non-finite node
             // is counted and contributes zero
@@ -286,12 +291,20 @@ __global__ void __launch_bounds__(kThreads)
                         acc[0] += ut * cs;
                         acc[1] -= ut * sn;
                     } else {
-                        acc[0] = fmax(acc[0], sqrt((double)ux * ux + (double)uy * uy));
-                        acc[1] = fmax(acc[1], fabs((double)dr));
+                        const float s32 = fmaf(ux, ux, uy * uy);
+                        if (s32 >= 0.9999f * m32) {
+                            m64 = fmax(m64, (double)ux * ux + (double)uy * uy);
+                            m32 = fmaxf(m32, s32);
+                        }
+                        dmax = fmaxf(dmax, fabsf(dr));
                     }
                 }
             }
             acc[3] += (double)bad;
+            if (WHAT == FDLBM_REDUCE_MAXABS) {
+                acc[0] = fmax(acc[0], sqrt(m64));
+                acc[1] = fmax(acc[1], (double)dmax);
+            }
             if (WHAT == FDLBM_REDUCE_MASS || WHAT == FDLBM_REDUCE_MOMENTUM) {
                 acc[0] += f0.flush();
                 acc[1] += f1.flush();
@@ -315,17 +328,33 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-__global__ void reduce_final_kernel(const double* __restrict__ partial, int nblocks, int what,
-                                    double* __restrict__ result) {
-    const int k = threadIdx.x;
-    if (k >= kReduceSlots) return;
-    const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
-    double v = is_max ? 0.0 : 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double p = partial[b * kReduceSlots + k];
-        v = is_max ? fmax(v, p) : v + p;
+constexpr int kFinalThreads = 128;
+
+// Combine the block partials: per slot, each thread folds a fixed strided
+// subset, then a fixed tree over the threads (deterministic order).
+__global__ void __launch_bounds__(kFinalThreads)
+    reduce_final_kernel(const double* __restrict__ partial, int nblocks, int what,
+                        double* __restrict__ result) {
+    __shared__ double sh[kFinalThreads / 32][kReduceSlots];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < kReduceSlots; ++k) {
+        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += kFinalThreads) {
+            const double p = partial[b * kReduceSlots + k];
+            v = is_max ? fmax(v, p) : v + p;
+        }
+        v = is_max ? warp_max(v) : warp_sum(v);
+        if (lane == 0) sh[wid][k] = v;
     }
-    result[k] = v;
+    __syncthreads();
+    if (threadIdx.x < kReduceSlots) {
+        const int k = threadIdx.x;
+        const bool is_max = what == FDLBM_REDUCE_MAXABS && k < 2;
+        double v = sh[0][k];
+        for (int w = 1; w < kFinalThreads / 32; ++w) v = is_max ? fmax(v, sh[w][k]) : v + sh[w][k];
+        result[k] = v;
+    }
 }
 
 template <typename F>
@@ -474,7 +503,8 @@ cudaError_t launch_reduce(fdlbm_s* h, const void* state, int what, double a0, do
     cudaError_t e = dispatch_kind(h, rl);
     if (e != cudaSuccess) return e;
     const dim3 g = reduce_grid(h->p.nx, h->p.ny);
-    reduce_final_kernel<<<1, 32, 0, h->stream>>>(partial, (int)(g.x * g.y), what, result);
+    reduce_final_kernel<<<1, kFinalThreads, 0, h->stream>>>(partial, (int)(g.x * g.y), what,
+                                                           result);
     return cudaGetLastError();
 }
 
