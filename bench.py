@@ -116,29 +116,50 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+# The translation unit of each profiled kernel; its hash covers the unit and
+# every header it includes (transitively), so a recorded DRAM figure is used
+# only while that kernel's code is unchanged.
+KERNEL_UNITS = {"fd_step": "fd_step_stream.cu", "mrt_step": "mrt_step.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    import re
     csrc = os.path.join(ROOT, "paper_1803_00437_gb300", "csrc")
+    inc = os.path.join(ROOT, "include")
+    seen, todo = [], [KERNEL_UNITS[kernel]]
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        seen.append(name)
+        for d in (csrc, inc):
+            path = os.path.join(d, name)
+            if os.path.exists(path):
+                with open(path) as fh:
+                    todo += re.findall(r'#include "([^"]+)"', fh.read())
+                break
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for name in sorted(seen):
+        for d in (csrc, inc):
+            path = os.path.join(d, name)
+            if os.path.exists(path):
+                with open(path, "rb") as fh:
+                    h.update(name.encode() + b"\0" + fh.read())
+                break
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, nodes: int):
     """DRAM bytes per launch from the committed ncu summary, scaled to `nodes`
-    node updates, or None if the kernels changed since it was taken."""
+    node updates, or None if the kernel changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(path) as fh:
             rec = json.loads("".join(ln for ln in fh if not ln.startswith("#")))
     except Exception:
         return None
-    if rec.get("source_hash") != kernel_source_hash():
-        return None
     k = rec.get("kernels", {}).get(kernel)
-    if not k:
+    if not k or k.get("source_hash") != kernel_source_hash(kernel):
         return None
     return k["dram_bytes_per_launch"] * nodes / k["nodes_per_launch"]
 
