@@ -69,11 +69,17 @@ extern "C" {
 #define FDLBM_STORAGE_F16 1  /* FD-LBM only: (rho-1, ux, uy) in FP16, FP32 math */
 #define FDLBM_STORAGE_BF16 2 /* FD-LBM only: (rho-1, ux, uy) in BF16, FP32 math */
 
-/* FD-LBM kernels: periodic lattices with nx % 8 == 0, nx >= 256, ny >= 16 use
- * the streaming kernel (TMA-staged rows, register window); every other case
- * uses the general tiled kernel.  FDLBM_FLAG_TILED forces the tiled kernel
- * (same results up to FP32 rounding; used to cross-check the two). */
+/* Kernel choice for FD-LBM lattices.  By default a lattice that qualifies
+ * for the streaming kernel (periodic or channel, nx % 8 == 0, nx >= 256,
+ * ny >= 16) and holds at least 2^20 nodes uses it; smaller or other
+ * lattices use the general tiled kernel, which spreads small lattices over
+ * more of the GPU (the streaming kernel walks each strip row by row and has
+ * a latency floor of ~18 us per step).  FDLBM_FLAG_TILED forces the tiled
+ * kernel; FDLBM_FLAG_STREAM forces the streaming kernel whenever the lattice
+ * qualifies (both give the same results up to FP32 rounding; used to
+ * cross-check the two).  Setting both is invalid. */
 #define FDLBM_FLAG_TILED 1
+#define FDLBM_FLAG_STREAM 2
 
 /* Parameters of one lattice.  Relaxation rates lie in (0, 2).
  *   s_xx : rate of XX and XY; shear viscosity nu = (1/s_xx - 1/2)/3 (Sec. 1-a)

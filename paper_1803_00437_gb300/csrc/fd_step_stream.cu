@@ -56,6 +56,7 @@ struct StreamArgs {
     size_t plane;     // elements per plane
     size_t pitch;     // elements per row
     int nx, ny;
+    float xi;         // wall offset (channels)
     int nstrips, seg_rows, nsegs, nitems;
     StreamCoeffs k;
     int* status;      // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
@@ -84,7 +85,21 @@ struct Item {
 // Issue rows k0 .. k0 + count - 1 (count 1 or 2) of the item into their ring
 // slots: lanes 0..count-1 first arm the rows' barriers with the byte count,
 // then lanes 0..3 count - 1 each copy one field of one row.
-template <typename T>
+// Channel (walls in y): a row outside [0, ny) is virtual (Sec. 3-b, 3-c
+// closure): its rho - 1 is the first fluid row's and its u the reference
+// row's (the first fluid row if xi >= 1/2, else the second) times the linear
+// extrapolation factor to u = 0 at the wall, applied when the row is read.
+__device__ __forceinline__ int wall_edge(int r, int ny) { return r < 0 ? 0 : ny - 1; }
+__device__ __forceinline__ int wall_ref(int r, int ny, float xi) {
+    return xi >= 0.5f ? wall_edge(r, ny) : (r < 0 ? 1 : ny - 2);
+}
+__device__ __forceinline__ float wall_factor(int r, int ny, float xi) {
+    if (r >= 0 && r < ny) return 1.f;
+    const float ywall = r < 0 ? -xi : (float)(ny - 1) + xi;
+    return ((float)r - ywall) / ((float)wall_ref(r, ny, xi) - ywall);
+}
+
+template <bool WALLS, typename T>
 __device__ __forceinline__ void issue_rows(const StreamArgs& a, const Ring<T>& ring,
                                            const Item& it, int k0, int count, int lane) {
     if (lane < count) {
@@ -98,8 +113,12 @@ __device__ __forceinline__ void issue_rows(const StreamArgs& a, const Ring<T>& r
         const int f = lane - 3 * j;       // which field
         const int slot = (it.base + k0 + j) & kSlotMask;
         int r = it.row_first + k0 + j;
-        if (r < 0) r += a.ny;
-        if (r >= a.ny) r -= a.ny;
+        if (!WALLS) {
+            if (r < 0) r += a.ny;
+            if (r >= a.ny) r -= a.ny;
+        } else if (r < 0 || r >= a.ny) {
+            r = f == 0 ? wall_edge(r, a.ny) : wall_ref(r, a.ny, a.xi);
+        }
         fence_proxy_async_smem();
         const T* rowp = static_cast<const T*>(a.src) + f * a.plane + (size_t)r * a.pitch;
         T* dst = slot_field(ring, slot, f);
@@ -124,7 +143,7 @@ __device__ __forceinline__ bool row_landed(const Ring<T>& ring, const Item& it, 
     return mbar_wait_bounded(&ring.bars[pos & kSlotMask], (pos / kSlots) & 1u);
 }
 
-template <int R, bool FORCE, typename T>
+template <int R, bool FORCE, bool WALLS, typename T>
 struct RowStep {
     // Field row k of the item (already landed): read it, update the y window
     // and reconstruct the centre row c = row k - R; close and store row c - 1.
@@ -141,6 +160,16 @@ struct RowStep {
         Vec4<T>::load(slot_field(ring, slot, 0) + col, nr);
         Vec4<T>::load(slot_field(ring, slot, 1) + col, nux);
         Vec4<T>::load(slot_field(ring, slot, 2) + col, nuy);
+        if (WALLS) {
+            const int r = it.row_first + k;
+            if (r < 0 || r >= a.ny) {  // uniform across the warp
+                const float2 fac = sp(wall_factor(r, a.ny, a.xi));
+                nux[0] = mul2(nux[0], fac);
+                nux[1] = mul2(nux[1], fac);
+                nuy[0] = mul2(nuy[0], fac);
+                nuy[1] = mul2(nuy[1], fac);
+            }
+        }
         Win nw;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -160,6 +189,16 @@ struct RowStep {
             if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
             Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
             Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
+            if (WALLS) {
+                const int r = it.row_first + k - R;
+                if (r < 0 || r >= a.ny) {
+                    const float2 fac = sp(wall_factor(r, a.ny, a.xi));
+                    cux[0] = mul2(cux[0], fac);
+                    cux[1] = mul2(cux[1], fac);
+                    cuy[0] = mul2(cuy[0], fac);
+                    cuy[1] = mul2(cuy[1], fac);
+                }
+            }
         }
         // Five points: the centre row's fields are rebuilt from the ring
         // (only the differences are held in registers).  Three points: the
@@ -288,7 +327,7 @@ struct RowStep {
     }
 };
 
-template <int R, bool FORCE, typename T>
+template <int R, bool FORCE, bool WALLS, typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
     fd_step_stream_kernel(StreamArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -325,12 +364,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
         __syncwarp();
         // prologue: the first kSlots rows, two per issue
         for (int k0 = 0; k0 < kSlots && k0 < it.nrows; k0 += 2)
-            issue_rows<T>(a, ring, it, k0, min(2, it.nrows - k0), lane);
+            issue_rows<WALLS, T>(a, ring, it, k0, min(2, it.nrows - k0), lane);
         issued = base + min(kSlots, it.nrows);
         Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
         Acc acc = {};
         int k = 0;
-        using Step = RowStep<R, FORCE, T>;
+        using Step = RowStep<R, FORCE, WALLS, T>;
         for (; k + 1 < it.nrows; k += 2) {
             // one vote for both rows keeps their arithmetic in one block,
             // free to interleave
@@ -353,7 +392,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
             const int n0 = (int)(issued - base);
             const int cnt = min(m1 + kSlots + 1, it.nrows) - n0;
             if (m1 >= 0 && cnt > 0) {
-                issue_rows<T>(a, ring, it, n0, cnt, lane);
+                issue_rows<WALLS, T>(a, ring, it, n0, cnt, lane);
                 issued += cnt;
             }
         }
@@ -408,9 +447,9 @@ Plan make_plan(int nx, int ny, int R, int resident_warps) {
     return best;
 }
 
-template <int R, bool FORCE, typename T>
+template <int R, bool FORCE, bool WALLS, typename T>
 cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
-    auto kernel = fd_step_stream_kernel<R, FORCE, T>;
+    auto kernel = fd_step_stream_kernel<R, FORCE, WALLS, T>;
     const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(T) + kSlots * 8);
     if (h->stream_plan_warps == 0) {
         cudaError_t e =
@@ -431,6 +470,7 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     a.pitch = h->L.pitch;
     a.nx = h->p.nx;
     a.ny = h->p.ny;
+    a.xi = (float)h->p.wall_xi;
     a.nstrips = (h->p.nx + kStrip - 1) / kStrip;
     a.seg_rows = plan.seg_rows;
     a.nsegs = plan.nsegs;
@@ -450,27 +490,34 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     return cudaGetLastError();
 }
 
-template <typename T>
+template <bool WALLS, typename T>
 cudaError_t launch_stream_stencil(fdlbm_s* h, const void* src, void* dst) {
     const bool force = h->p.force_x != 0.0 || h->p.force_y != 0.0;
     if (h->p.scheme == FDLBM_SCHEME_FD3)
-        return force ? launch_stream_typed<1, true, T>(h, src, dst)
-                     : launch_stream_typed<1, false, T>(h, src, dst);
-    return force ? launch_stream_typed<2, true, T>(h, src, dst)
-                 : launch_stream_typed<2, false, T>(h, src, dst);
+        return force ? launch_stream_typed<1, true, WALLS, T>(h, src, dst)
+                     : launch_stream_typed<1, false, WALLS, T>(h, src, dst);
+    return force ? launch_stream_typed<2, true, WALLS, T>(h, src, dst)
+                 : launch_stream_typed<2, false, WALLS, T>(h, src, dst);
+}
+
+template <typename T>
+cudaError_t launch_stream_boundary(fdlbm_s* h, const void* src, void* dst) {
+    return h->p.boundary == FDLBM_BOUNDARY_WALLS_Y ? launch_stream_stencil<true, T>(h, src, dst)
+                                                   : launch_stream_stencil<false, T>(h, src, dst);
 }
 
 }  // namespace
 
 bool fd_stream_supported(const fdlbm_params& p) {
-    return p.boundary == FDLBM_BOUNDARY_PERIODIC && p.nx % 8 == 0 && p.nx >= 256 && p.ny >= 16;
+    return (p.boundary == FDLBM_BOUNDARY_PERIODIC || p.boundary == FDLBM_BOUNDARY_WALLS_Y) &&
+           p.nx % 8 == 0 && p.nx >= 256 && p.ny >= 16;
 }
 
 cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst) {
     switch (h->p.storage) {
-        case FDLBM_STORAGE_F16: return launch_stream_stencil<__half>(h, src, dst);
-        case FDLBM_STORAGE_BF16: return launch_stream_stencil<__nv_bfloat16>(h, src, dst);
-        default: return launch_stream_stencil<float>(h, src, dst);
+        case FDLBM_STORAGE_F16: return launch_stream_boundary<__half>(h, src, dst);
+        case FDLBM_STORAGE_BF16: return launch_stream_boundary<__nv_bfloat16>(h, src, dst);
+        default: return launch_stream_boundary<float>(h, src, dst);
     }
 }
 

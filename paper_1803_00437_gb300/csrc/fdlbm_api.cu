@@ -55,7 +55,10 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->storage != FDLBM_STORAGE_F32 && p->storage != FDLBM_STORAGE_F16 &&
         p->storage != FDLBM_STORAGE_BF16)
         return fail(FDLBM_ERR_INVALID, "storage must be F32, F16 or BF16");
-    if ((p->flags & ~FDLBM_FLAG_TILED) != 0) return fail(FDLBM_ERR_INVALID, "unknown flags");
+    if ((p->flags & ~(FDLBM_FLAG_TILED | FDLBM_FLAG_STREAM)) != 0)
+        return fail(FDLBM_ERR_INVALID, "unknown flags");
+    if ((p->flags & FDLBM_FLAG_TILED) && (p->flags & FDLBM_FLAG_STREAM))
+        return fail(FDLBM_ERR_INVALID, "FDLBM_FLAG_TILED and FDLBM_FLAG_STREAM exclude each other");
     if (!valid_rate(p->s_xx) || !valid_rate(p->s_e))
         return fail(FDLBM_ERR_INVALID, "s_xx and s_e must lie in (0, 2)");
     if (p->scheme == FDLBM_SCHEME_MRT && (!valid_rate(p->s_q) || !valid_rate(p->s_eps)))
@@ -178,7 +181,7 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
     h->cur = 0;
     h->launches = 0;
     h->stream_plan_warps = 0;
-    h->fd_path = (p->flags & FDLBM_FLAG_TILED) ? 1 : 0;
+    h->fd_path = (p->flags & FDLBM_FLAG_TILED) ? 1 : (p->flags & FDLBM_FLAG_STREAM) ? 2 : 0;
     h->err[0] = 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         delete h;
@@ -435,7 +438,11 @@ int64_t fdlbm_launch_count(const fdlbm_t* h) { return h ? h->launches : -1; }
 
 namespace fdlbm {
 cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
-    if (h->fd_path == 0 && fd_stream_supported(h->p)) return launch_fd_step_stream(h, src, dst);
+    // the streaming kernel pays off once the lattice fills the GPU's warps
+    constexpr int64_t kStreamMinNodes = 1 << 20;
+    const bool big = (int64_t)h->p.nx * h->p.ny >= kStreamMinNodes;
+    if (h->fd_path != 1 && fd_stream_supported(h->p) && (big || h->fd_path == 2))
+        return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }
 }  // namespace fdlbm

@@ -102,7 +102,7 @@ struct fdlbm_s {
     int cur;  // index of the current state copy
     int64_t launches;
     int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
-    int fd_path;            // 0: automatic, 1: force the tiled FD kernel
+    int fd_path;            // 0: automatic, 1: tiled FD kernel, 2: streaming where it qualifies
     // page-locked host landing area for reduction results and the device
     // status word (one synchronisation per reduction); NULL if unavailable
     struct HostIO {

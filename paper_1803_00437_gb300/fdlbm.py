@@ -25,6 +25,7 @@ BOUNDARIES = {"periodic": 0, "walls_y": 1}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}
 FLAG_TILED = 1
+FLAG_STREAM = 2
 
 
 class FdlbmError(RuntimeError):

@@ -330,21 +330,41 @@ def test_streaming_kernel_parity(oracle, scheme, shape):
     d, ux, uy = inputs.transverse_modes(nx, ny, modes)
     d = inputs.random_fields(nx, ny, 0.0, seed=3, rho_amp=1e-3)[0]
     f = as_f32((d, ux, uy))
-    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.01), s_e=1.5)
+    from paper_1803_00437_gb300 import fdlbm as F
+    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.01), s_e=1.5, flags=F.FLAG_STREAM)
     gpu, _ = gpu_run(cfg, f, 200)
     ref = oracle_run(oracle, cfg, f, 200)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("scheme,shape,xi", [("fd5", (256, 24), 0.5), ("fd5", (264, 37), 0.3),
+                                              ("fd3", (256, 40), 1.0), ("fd5", (512, 64), 0.8),
+                                              ("fd3", (264, 17), 0.3)])
+def test_streaming_channel_parity(oracle, scheme, shape, xi):
+    """Channels (walls in y, periodic in x) taking the streaming kernel:
+    virtual rows below and above fed from the edge / reference rows with the
+    extrapolation factor, body force, several strips and row segments, a
+    partial last strip and odd heights; seeded non-uniform start, 300 steps."""
+    nx, ny = shape
+    f = as_f32(inputs.random_fields(nx, ny, 0.01, seed=nx * 7 + ny, rho_amp=0.002))
+    from paper_1803_00437_gb300 import fdlbm as F
+    cfg = _cfg(nx, ny, scheme, s_xx=_nu(1 / np.sqrt(108)), s_e=1.5, boundary="walls_y",
+               wall_xi=xi, force=(2e-5, -1e-6), flags=F.FLAG_STREAM)
+    gpu, _ = gpu_run(cfg, f, 300)
+    ref = oracle_run(oracle, cfg, f, 300)
     assert max_err(gpu, ref, amplitude(f)) <= TOL32
 
 
 @pytest.mark.parametrize("scheme", ["fd3", "fd5"])
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_streaming_equals_tiled(scheme, storage):
-    """Both FD-LBM kernels give the same lattice (FP32 arithmetic in both;
-    they differ only in the order of roundings)."""
+    """Both FD-LBM kernels give the same lattice, periodic and channel (FP32
+    arithmetic in both; they differ only in the order of roundings)."""
     nx, ny = 392, 72
     f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=8, rho_amp=0.005))
     from paper_1803_00437_gb300 import fdlbm as F
-    a, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage), f, 30)
-    b, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage, flags=F.FLAG_TILED), f, 30)
     tol = {"f32": 1e-5, "f16": 2e-2, "bf16": 1e-1}[storage]
-    assert max_err(a, b, amplitude(f)) <= tol
+    for kw in ({}, dict(boundary="walls_y", wall_xi=0.4, force=(1e-5, 0.0))):
+        a, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage, flags=F.FLAG_STREAM, **kw), f, 30)
+        b, _ = gpu_run(_cfg(nx, ny, scheme, storage=storage, flags=F.FLAG_TILED, **kw), f, 30)
+        assert max_err(a, b, amplitude(f)) <= tol, kw
