@@ -5,7 +5,8 @@
 Builds the library if needed, initialises a periodic side x side lattice
 with 32 seeded transverse modes (amplitude 1e-3, nu = 0.01, s_e = 1.5),
 advances it, and prints one JSON line (steps, milliseconds per step, MLUPS,
-max |u|).  Used to drive profiler captures of a single kernel.
+max |u| and any FP64 reductions asked for with --reduce).  Used to drive
+profiler captures of a single kernel.
 """
 from __future__ import annotations
 
@@ -21,6 +22,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--nu", type=float, default=0.01)
     ap.add_argument("--modes", type=int, default=32)
+    ap.add_argument("--reduce", nargs="*", default=[],
+                    choices=["mass", "momentum", "energy", "maxabs"],
+                    help="FP64 reductions of the final state to report")
     args = ap.parse_args(argv)
 
     import torch
@@ -37,10 +41,11 @@ def main(argv=None):
     e1.record(lat.stream)
     lat.sync()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    reductions = {w: [float(v) for v in lat.reduce(w)] for w in args.reduce}
     print(json.dumps({"side": n, "scheme": args.scheme, "storage": args.storage,
                       "steps": args.steps, "ms_per_step": round(ms, 4),
                       "mlups": round(n * n / ms / 1e3, 1),
-                      "max_u": float(lat.reduce("maxabs")[0])}))
+                      "max_u": float(lat.reduce("maxabs")[0]), "reductions": reductions}))
 
 
 if __name__ == "__main__":
