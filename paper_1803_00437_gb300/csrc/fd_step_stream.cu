@@ -1,5 +1,5 @@
-// fd_step_stream.cu -- FD-LBM step (Sec. 2, Eq. 2) for periodic lattices,
-// streaming each warp down a strip of rows.
+// fd_step_stream.cu -- FD-LBM step (Sec. 2, Eq. 2) for lattices periodic in
+// x (periodic or walled in y), streaming each warp down a strip of rows.
 //
 // Work decomposition.  A warp owns an output strip of 120 columns and a
 // segment of rows.  Lane L holds 4 consecutive columns starting at
