@@ -1,5 +1,6 @@
 /*
- * fdlbm_ref.c -- FP64 CPU oracle: FD-LBM (Sec. 2) and MRT D2Q9 (Sec. 1-a).
+ * fdlbm_ref.c -- FP64 CPU oracle: FD-LBM (Sec. 2), MRT D2Q9 (Sec. 1-a) and the
+ * link-wise artificial compressibility method LW-ACM (Sec. 1-b, Eq. 3).
  *
  * TEST INFRASTRUCTURE ONLY (see fdlbm_ref.h).  Written for a reader who
  * checks it against the paper by eye: the moment matrix M is the table of
@@ -25,6 +26,13 @@
  *   - Force: Strang splitting on J only.  J' = J + F/2 enters the equilibria
  *     and theta; the post-collision momentum is J' + F/2; the stored velocity
  *     is u = J' / rho.
+ *   - LW-ACM, Eq. 3: the odd part of the equilibrium f^eo(i0, j0) is taken
+ *     at the node the link points to, (i0, j0) = (i, j) + c_a, before the
+ *     propagation; after it, f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) -
+ *     feo_a(x - c_a)).  This placement gives the H(k) printed in Sec. 1-b
+ *     (its (1,2) entry -6 i nu k); the upstream node would give
+ *     -i k (1 + Theta) / 3.  The equilibrium is the second-order D2Q9 one in
+ *     (rho, u); periodic, no force (the paper gives neither for it).
  *   - Walls (Sec. 3-b, 3-c): virtual nodes outside the fluid carry u linearly
  *     extrapolated to zero at the wall, from the first fluid row when
  *     xi >= 1/2 and from the second when xi < 1/2; rho is copied from the
@@ -93,7 +101,7 @@ static int valid_params(const fdlbm_ref_params* p) {
     if (!p) return 0;
     if (p->nx < 1 || p->ny < 1) return 0;
     if (p->scheme != FDLBM_REF_FD3 && p->scheme != FDLBM_REF_FD5 && p->scheme != FDLBM_REF_FD9 &&
-        p->scheme != FDLBM_REF_MRT)
+        p->scheme != FDLBM_REF_MRT && p->scheme != FDLBM_REF_LWACM)
         return 0;
     if (p->boundary != FDLBM_REF_PERIODIC && p->boundary != FDLBM_REF_WALLS_Y) return 0;
     if (!(p->s_xx > 0.0 && p->s_xx < 2.0)) return 0;
@@ -514,6 +522,113 @@ int fdlbm_ref_mrt_step_points_from_eq(const fdlbm_ref_params* p, const double* r
             f[a] = fo[pa];
         }
         close_moments(p, f, &out[3 * t], &out[3 * t + 1], &out[3 * t + 2]);
+    }
+    return FDLBM_REF_OK;
+}
+
+/* ---- LW-ACM (Sec. 1-b) ------------------------------------------------------ */
+
+/* D2Q9 weights of the equilibrium (Sec. 1, the f^eq identity). */
+static const double W[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                            1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+
+/* Second-order equilibrium of population a for density r and velocity (vx, vy). */
+static double lw_feq(int a, double r, double vx, double vy) {
+    const double cu = CX[a] * vx + CY[a] * vy;
+    const double u2 = vx * vx + vy * vy;
+    return W[a] * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2);
+}
+
+/* Odd part of the equilibrium: (feq(r, u) - feq(r, -u)) / 2. */
+static double lw_feo(int a, double r, double vx, double vy) {
+    return 0.5 * (lw_feq(a, r, vx, vy) - lw_feq(a, r, -vx, -vy));
+}
+
+static int lw_valid(const fdlbm_ref_params* p) {
+    return valid_params(p) && p->scheme == FDLBM_REF_LWACM &&
+           p->boundary == FDLBM_REF_PERIODIC && p->force_x == 0.0 && p->force_y == 0.0;
+}
+
+/* Theta = 1 - 2 nu / c_s^2 = 1 - 6 nu, nu = (1/s_xx - 1/2) / 3 */
+static double lw_theta(const fdlbm_ref_params* p) {
+    const double nu = (1.0 / p->s_xx - 0.5) / 3.0;
+    return 1.0 - 6.0 * nu;
+}
+
+static void lw_moments(const double f[9], double* r, double* vx, double* vy) {
+    double s = 0.0, jx = 0.0, jy = 0.0;
+    for (int a = 0; a < 9; ++a) {
+        s += f[a];
+        jx += CX[a] * f[a];
+        jy += CY[a] * f[a];
+    }
+    *r = s;
+    *vx = jx / s;
+    *vy = jy / s;
+}
+
+int fdlbm_ref_lwacm_step(const fdlbm_ref_params* p, double* rho, double* ux, double* uy,
+                         int64_t nsteps) {
+    if (!lw_valid(p) || !rho || !ux || !uy || nsteps < 0) return FDLBM_REF_EINVAL;
+    const int nx = p->nx, ny = p->ny;
+    const int64_t plane = (int64_t)nx * ny;
+    double* fstar = (double*)malloc(sizeof(double) * 9 * (size_t)plane);
+    if (!fstar) return FDLBM_REF_ENOMEM;
+    const double theta = lw_theta(p);
+    const int nthr = fdlbm_ref_get_threads();
+    (void)nthr;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        /* reconstruction at every node, from the equilibria of the node and of
+           the node each link points to */
+#pragma omp parallel for schedule(static) num_threads(nthr)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                const int64_t o = (int64_t)j * nx + i;
+                for (int a = 0; a < 9; ++a) {
+                    const int64_t d = (int64_t)wrap(j + CY[a], ny) * nx + wrap(i + CX[a], nx);
+                    fstar[a * plane + o] =
+                        lw_feq(a, rho[o], ux[o], uy[o]) +
+                        theta * (lw_feo(a, rho[d], ux[d], uy[d]) - lw_feo(a, rho[o], ux[o], uy[o]));
+                }
+            }
+        }
+        /* propagation and moments */
+#pragma omp parallel for schedule(static) num_threads(nthr)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                double f[9];
+                for (int a = 0; a < 9; ++a)
+                    f[a] = fstar[a * plane + (int64_t)wrap(j - CY[a], ny) * nx + wrap(i - CX[a], nx)];
+                const int64_t o = (int64_t)j * nx + i;
+                lw_moments(f, &rho[o], &ux[o], &uy[o]);
+            }
+        }
+    }
+    free(fstar);
+    return FDLBM_REF_OK;
+}
+
+int fdlbm_ref_lwacm_step_points(const fdlbm_ref_params* p, const double* rho, const double* ux,
+                                const double* uy, int64_t npts, const int64_t* idx, double* out) {
+    if (!lw_valid(p) || !rho || !ux || !uy || npts < 0 || (npts > 0 && (!idx || !out)))
+        return FDLBM_REF_EINVAL;
+    const int nx = p->nx, ny = p->ny;
+    for (int64_t t = 0; t < npts; ++t)
+        if (idx[t] < 0 || idx[t] >= (int64_t)nx * ny) return FDLBM_REF_EINVAL;
+    const double theta = lw_theta(p);
+    const int nthr = fdlbm_ref_get_threads();
+    (void)nthr;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthr)
+    for (int64_t t = 0; t < npts; ++t) {
+        const int i = (int)(idx[t] % nx), j = (int)(idx[t] / nx);
+        const int64_t x = idx[t];
+        double f[9];
+        for (int a = 0; a < 9; ++a) {
+            const int64_t y = (int64_t)wrap(j - CY[a], ny) * nx + wrap(i - CX[a], nx);
+            f[a] = lw_feq(a, rho[y], ux[y], uy[y]) +
+                   theta * (lw_feo(a, rho[x], ux[x], uy[x]) - lw_feo(a, rho[y], ux[y], uy[y]));
+        }
+        lw_moments(f, &out[3 * t], &out[3 * t + 1], &out[3 * t + 2]);
     }
     return FDLBM_REF_OK;
 }

@@ -36,6 +36,7 @@ extern "C" {
 #define FDLBM_REF_FD5 5     /* five-point centred difference   */
 #define FDLBM_REF_FD9 9     /* nine-point D2Q9-footprint difference */
 #define FDLBM_REF_MRT 100   /* multiple-relaxation-time D2Q9 LBM */
+#define FDLBM_REF_LWACM 200 /* link-wise artificial compressibility method (Sec. 1-b) */
 
 /* boundary */
 #define FDLBM_REF_PERIODIC 0
@@ -47,7 +48,7 @@ extern "C" {
 
 typedef struct {
     int32_t nx, ny;
-    int32_t scheme;    /* FDLBM_REF_FD3 / FD5 / FD9 / MRT */
+    int32_t scheme;    /* FDLBM_REF_FD3 / FD5 / FD9 / MRT / LWACM */
     int32_t boundary;  /* FDLBM_REF_PERIODIC / WALLS_Y */
     double s_xx;       /* rate of XX and XY (shear viscosity) */
     double s_e;        /* rate of E (bulk viscosity) */
@@ -95,6 +96,23 @@ int fdlbm_ref_mrt_moments(const fdlbm_ref_params* p, const double* f, double* rh
 int fdlbm_ref_mrt_step_points_from_eq(const fdlbm_ref_params* p, const double* rho,
                                       const double* ux, const double* uy, int64_t npts,
                                       const int64_t* idx, double* out);
+
+/* LW-ACM (Sec. 1-b, Eq. 3): nsteps steps of the (rho, ux, uy) state in place.
+ * Reconstruction at each node from the equilibria alone,
+ *   f*_a(x) = feq_a(x) + Theta (feo_a(x + c_a) - feo_a(x)),
+ * feo the odd part of feq, Theta = 1 - 6 nu with nu = (1/s_xx - 1/2) / 3,
+ * then propagation f_a(x + c_a) <- f*_a(x) and the moments.  Periodic
+ * lattices without force only (the paper gives neither walls nor a force
+ * for this scheme); s_e is not used. */
+int fdlbm_ref_lwacm_step(const fdlbm_ref_params* p, double* rho, double* ux, double* uy,
+                         int64_t nsteps);
+
+/* LW-ACM: one step evaluated only at the nodes idx[0..npts) (flat j*nx + i),
+ * with the propagation substituted into the reconstruction:
+ *   f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) - feo_a(x - c_a)).
+ * out[3 t + 0..2] = (rho, ux, uy) at idx[t]. */
+int fdlbm_ref_lwacm_step_points(const fdlbm_ref_params* p, const double* rho, const double* ux,
+                                const double* uy, int64_t npts, const int64_t* idx, double* out);
 
 #ifdef __cplusplus
 }

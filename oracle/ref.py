@@ -22,7 +22,7 @@ SRC = os.path.join(HERE, "fdlbm_ref.c")
 HDR = os.path.join(HERE, "fdlbm_ref.h")
 LIB = os.path.join(HERE, "libfdlbm_ref.so")
 
-FD3, FD5, FD9, MRT = 3, 5, 9, 100
+FD3, FD5, FD9, MRT, LWACM = 3, 5, 9, 100, 200
 PERIODIC, WALLS_Y = 0, 1
 
 _lock = threading.Lock()
@@ -73,9 +73,12 @@ def lib():
             L.fdlbm_ref_mrt_moments.argtypes = [pp, dp, dp, dp, dp]
             L.fdlbm_ref_mrt_step_points_from_eq.argtypes = [pp, dp, dp, dp, ctypes.c_int64,
                                                              i64p, dp]
+            L.fdlbm_ref_lwacm_step.argtypes = [pp, dp, dp, dp, ctypes.c_int64]
+            L.fdlbm_ref_lwacm_step_points.argtypes = [pp, dp, dp, dp, ctypes.c_int64, i64p, dp]
             for name in ("fdlbm_ref_fd_step", "fdlbm_ref_fd_step_points", "fdlbm_ref_fd_fstar",
                          "fdlbm_ref_mrt_init", "fdlbm_ref_mrt_step", "fdlbm_ref_mrt_moments",
-                         "fdlbm_ref_mrt_step_points_from_eq"):
+                         "fdlbm_ref_mrt_step_points_from_eq", "fdlbm_ref_lwacm_step",
+                         "fdlbm_ref_lwacm_step_points"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -190,8 +193,31 @@ def mrt_step_points_from_eq(p: Params, rho, ux, uy, idx):
     return out
 
 
+def lwacm_run(p: Params, rho, ux, uy, nsteps: int):
+    """LW-ACM (Sec. 1-b): return (rho, ux, uy) after nsteps, FP64 copies of the inputs."""
+    shape = (p.ny, p.nx)
+    r, x, y = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
+    _check(lib().fdlbm_ref_lwacm_step(ctypes.byref(p), _dptr(r), _dptr(x), _dptr(y),
+                                      int(nsteps)), "lwacm_step")
+    return r, x, y
+
+
+def lwacm_step_points(p: Params, rho, ux, uy, idx):
+    shape = (p.ny, p.nx)
+    r, x, y = (np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ux, uy))
+    assert r.shape == shape and x.shape == shape and y.shape == shape
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((idx.size, 3))
+    _check(lib().fdlbm_ref_lwacm_step_points(
+        ctypes.byref(p), _dptr(r), _dptr(x), _dptr(y), idx.size,
+        idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(out)), "lwacm_step_points")
+    return out
+
+
 def run(p: Params, rho, ux, uy, nsteps: int):
-    """Either scheme from primitive fields; returns (rho, ux, uy)."""
+    """Any scheme from primitive fields; returns (rho, ux, uy)."""
     if p.scheme == MRT:
         return mrt_run(p, rho, ux, uy, nsteps)
+    if p.scheme == LWACM:
+        return lwacm_run(p, rho, ux, uy, nsteps)
     return fd_run(p, rho, ux, uy, nsteps)

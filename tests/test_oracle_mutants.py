@@ -31,6 +31,20 @@ MUTANTS = {
     "half_force": ("m[1] = Jx + 0.5 * p->force_x;", "m[1] = Jx;"),
 }
 
+# LW-ACM (Sec. 1-b), checked by its own pins
+LW_MUTANTS = {
+    # odd part taken at the upstream node instead of the node the link points to
+    "lw_upstream": ("const int64_t d = (int64_t)wrap(j + CY[a], ny) * nx + wrap(i + CX[a], nx);",
+                    "const int64_t d = (int64_t)wrap(j - CY[a], ny) * nx + wrap(i - CX[a], nx);"),
+    # Theta = 1 - 2 nu / c_s^2 with c_s^2 = 2/3 instead of 1/3
+    "lw_theta": ("return 1.0 - 6.0 * nu;", "return 1.0 - 3.0 * nu;"),
+    # equilibrium without its quadratic term
+    "lw_quadratic": ("1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * u2", "1.0 + 3.0 * cu - 1.5 * u2"),
+    # even part instead of the odd part
+    "lw_even_part": ("return 0.5 * (lw_feq(a, r, vx, vy) - lw_feq(a, r, -vx, -vy));",
+                     "return 0.5 * (lw_feq(a, r, vx, vy) + lw_feq(a, r, -vx, -vy));"),
+}
+
 
 def _build(tmp, name, old, new):
     src = open(SRC).read()
@@ -107,6 +121,27 @@ def oracle_at(tmp_path):
     ref.LIB = os.path.join(ROOT, "oracle", "libfdlbm_ref.so")
 
 
+def _lw_pins_pass(ref):
+    """The LW-ACM pins (see test_oracle_lwacm): printed H(k), sound, nu(v),
+    conservation."""
+    import test_oracle_lwacm as T
+    failures = []
+    B, k, _ = T._jacobian(ref, 64, 4, 1, 0, 0.02)
+    if np.abs(B - T._printed_H(k, 0.02)).max() > k ** 3:
+        failures.append("printed_H")
+    B, k, _ = T._jacobian(ref, 128, 4, 1, 0, 0.02, V=(0.1, 0.0))
+    w, vecs = np.linalg.eig(B)
+    shear = w[np.argmax(np.abs(vecs[2, :]))]
+    if abs(-np.log(abs(shear)) / ((0.02 - 0.005) * k * k) - 1) > 0.02:
+        failures.append("nu_of_v")
+    p = ref.params(24, 20, ref.LWACM, T._s(0.02))
+    d, ux, uy = inputs.random_fields(24, 20, 0.02, seed=6, rho_amp=0.01)
+    r, x, y = ref.lwacm_run(p, 1 + d, ux, uy, 50)
+    if abs(r.sum() - (1 + d).sum()) > 1e-10 or abs((r * x).sum() - ((1 + d) * ux).sum()) > 1e-10:
+        failures.append("conservation")
+    return failures
+
+
 def test_unmodified_oracle_passes_the_pins(oracle_at):
     from oracle import ref
     ref.build()
@@ -118,4 +153,18 @@ def test_planted_mistake_is_caught(tmp_path, oracle_at, name):
     old, new = MUTANTS[name]
     lib = _build(tmp_path, name, old, new)
     failures = _pins_pass(oracle_at(lib))
+    assert failures, f"mutant {name} passed every pin"
+
+
+def test_unmodified_lwacm_oracle_passes_its_pins(oracle_at):
+    from oracle import ref
+    ref.build()
+    assert _lw_pins_pass(oracle_at(os.path.join(ROOT, "oracle", "libfdlbm_ref.so"))) == []
+
+
+@pytest.mark.parametrize("name", sorted(LW_MUTANTS))
+def test_planted_lwacm_mistake_is_caught(tmp_path, oracle_at, name):
+    old, new = LW_MUTANTS[name]
+    lib = _build(tmp_path, name, old, new)
+    failures = _lw_pins_pass(oracle_at(lib))
     assert failures, f"mutant {name} passed every pin"
