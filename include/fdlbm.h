@@ -60,6 +60,13 @@ extern "C" {
 #define FDLBM_SCHEME_FD3 3   /* FD-LBM, three-point differences (Sec. 2)   */
 #define FDLBM_SCHEME_FD5 5   /* FD-LBM, five-point differences (Sec. 2)    */
 #define FDLBM_SCHEME_MRT 100 /* multiple-relaxation-time D2Q9 (Sec. 1-a)  */
+/* Link-wise artificial compressibility method (Sec. 1-b, Eq. 3): every link
+ * rebuilt from equilibria alone, f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) -
+ * feo_a(x - c_a)), feo the odd part of feq, Theta = 1 - 6 nu, nu from s_xx as
+ * for the other schemes; s_e is not used.  Same (rho - 1, ux, uy) state and
+ * storage options as FD-LBM.  Periodic lattices with nx % 8 == 0, nx >= 256,
+ * ny >= 16, no force (FDLBM_ERR_UNSUPPORTED otherwise). */
+#define FDLBM_SCHEME_LWACM 200
 
 #define FDLBM_BOUNDARY_PERIODIC 0 /* periodic in x and y                  */
 #define FDLBM_BOUNDARY_WALLS_Y 1  /* periodic in x; walls below row 0 and

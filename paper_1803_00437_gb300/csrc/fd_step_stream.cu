@@ -185,7 +185,13 @@ struct RowStep {
         const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
-        if (!WARM || k >= R) {
+        if (R == 0) {  // LW-ACM: no derivative window, the new row is the centre
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                cux[h] = nux[h];
+                cuy[h] = nuy[h];
+            }
+        } else if (!WARM || k >= R) {
             if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
             Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
             Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
@@ -215,7 +221,7 @@ struct RowStep {
                 rebuilt.v[W_PYY][h] = mul2(jy, cuy[h]);
             }
         }
-        const Win& cen = (R == 1) ? fm1 : rebuilt;
+        const Win& cen = (R == 0) ? nw : (R == 1) ? fm1 : rebuilt;
         // y derivatives at the centre row (scaled by 2 or 8):
         //   three points: 2 d/dy = f(c+1) - f(c-1)
         //   five points:  8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), d1(c+1) = f(r) - f(c);
@@ -226,7 +232,9 @@ struct RowStep {
         for (int f = 0; f < W_N; ++f)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                if (R == 1) {
+                if (R == 0) {
+                    dy.v[f][h] = sp(0.f);  // unused
+                } else if (R == 1) {
                     dy.v[f][h] = sub2(nw.v[f][h], fm2.v[f][h]);
                 } else {
                     d1new.v[f][h] = sub2(cen.v[f][h], nw.v[f][h]);
@@ -237,19 +245,25 @@ struct RowStep {
         float2 pxx[2], dxr[2], dxjx[2], dxjy[2], dxpxx[2], dxpxy[2];
         pxx[0] = mul2(cen.v[W_JX][0], cux[0]);
         pxx[1] = mul2(cen.v[W_JX][1], cux[1]);
-        deriv_x<R>(cen.v[W_R], dxr);
-        deriv_x<R>(cen.v[W_JX], dxjx);
-        deriv_x<R>(cen.v[W_JY], dxjy);
-        deriv_x<R>(pxx, dxpxx);
-        deriv_x<R>(cen.v[W_PXY], dxpxy);
-
         float2 g[2][9];
+        if (R == 0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-            reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
+            for (int h = 0; h < 2; ++h)
+                reconstruct_lw2(cen.v[W_R][h], cen.v[W_JX][h], cen.v[W_JY][h], pxx[h],
+                                cen.v[W_PXY][h], cen.v[W_PYY][h], a.k, g[h]);
+        } else {
+            deriv_x<R>(cen.v[W_R], dxr);
+            deriv_x<R>(cen.v[W_JX], dxjx);
+            deriv_x<R>(cen.v[W_JY], dxjy);
+            deriv_x<R>(pxx, dxpxx);
+            deriv_x<R>(cen.v[W_PXY], dxpxy);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
                                 pxx[h], cen.v[W_PXY][h], cen.v[W_PYY][h], dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
                                 dy.v[W_JY][h], dxpxx[h], dxpxy[h], dy.v[W_PXY][h],
                                 dy.v[W_PYY][h], a.k, g[h]);
+        }
 
         // populations crossing lane boundaries: right-going (1, 5, 8) of
         // column 3 to the next lane, left-going (3, 6, 7) of column 0 back
@@ -302,6 +316,15 @@ struct RowStep {
                 px = add2(px, sp(a.k.hfx));
                 py = add2(py, sp(a.k.hfy));
             }
+            if (R == 0) {
+                // LW-ACM: Theta J = J - 3 t of the closing row (the previous
+                // row), t = 2 nu J the same product that row sent to its
+                // neighbours, so the momentum leaving and entering cancel
+                const float2 tx = mul2(fm1.v[W_JX][h], sp(a.k.lw_t));
+                const float2 ty = mul2(fm1.v[W_JY][h], sp(a.k.lw_t));
+                px = add2(px, fma2(sp(-3.f), tx, fm1.v[W_JX][h]));
+                py = add2(py, fma2(sp(-3.f), ty, fm1.v[W_JY][h]));
+            }
             const float2 nrho = fma2(drn, sp(-1.f), sp(-1.f));  // -(1 + dr)
             const float2 ninv = make_float2(rcp_approx(nrho.x), rcp_approx(nrho.y));
             odr[h] = drn;
@@ -322,7 +345,7 @@ struct RowStep {
             Vec4<T>::store(dst + 2 * a.plane, ouy);
         }
         // rotate the window: the oldest row/difference take the new ones
-        if (R == 1) fm2 = nw;
+        if (R <= 1) fm2 = nw;
         if (R == 2) dm3 = d1new;
     }
 };
@@ -485,6 +508,9 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     a.k.x13 = (float)(axx / 3.0);
     a.k.hfx = (float)(0.5 * h->p.force_x);
     a.k.hfy = (float)(0.5 * h->p.force_y);
+    const double nu = (1.0 / h->p.s_xx - 0.5) / 3.0;  // LW-ACM (Sec. 1-b)
+    a.k.lw_t = (float)(2.0 * nu);
+    a.k.lw_s = a.k.lw_t * 0.25f;
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
     kernel<<<plan.blocks, kWarpsPerBlock * 32, smem, h->stream>>>(a);
     return cudaGetLastError();
@@ -493,6 +519,8 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
 template <bool WALLS, typename T>
 cudaError_t launch_stream_stencil(fdlbm_s* h, const void* src, void* dst) {
     const bool force = h->p.force_x != 0.0 || h->p.force_y != 0.0;
+    // LW-ACM: no finite differences (radius 0), periodic, no force
+    if (h->p.scheme == FDLBM_SCHEME_LWACM) return launch_stream_typed<0, false, false, T>(h, src, dst);
     if (h->p.scheme == FDLBM_SCHEME_FD3)
         return force ? launch_stream_typed<1, true, WALLS, T>(h, src, dst)
                      : launch_stream_typed<1, false, WALLS, T>(h, src, dst);

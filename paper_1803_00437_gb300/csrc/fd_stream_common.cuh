@@ -95,6 +95,7 @@ struct StreamCoeffs {
     float e6, e2, em2;  // theta_E terms, times (1 - 1/s_e) / (36 scale)
     float xm23, x13;    // -2/3 and 1/3, times (1 - 1/s_xx) / scale (theta_XX, theta_XY)
     float hfx, hfy;            // half of the body force
+    float lw_t, lw_s;          // LW-ACM: 2 nu and nu / 2 (exactly lw_t / 4)
 };
 
 // x-derivative (scaled by 2 or 8) at the 4 columns of this lane.
@@ -171,6 +172,42 @@ __device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, fl
     const float2 ax = fma2(xx, sp(0.25f), axis), ay = fma2(xx, sp(-0.25f), axis);
     const float2 dp = fma2(xy, sp(0.25f), diag), dm = fma2(xy, sp(-0.25f), diag);
     const float2 spp = add2(sx, sy), smm = sub2(sy, sx);
+    g[1] = add2(ax, tx);
+    g[3] = sub2(ax, tx);
+    g[2] = add2(ay, ty);
+    g[4] = sub2(ay, ty);
+    g[5] = add2(dp, spp);
+    g[7] = sub2(dp, spp);
+    g[6] = add2(dm, smm);
+    g[8] = sub2(dm, smm);
+}
+
+// LW-ACM reconstruction (Sec. 1-b, Eq. 3) of two columns.  After the
+// propagation f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) - feo_a(x - c_a)),
+// so the new moments gather h_a = feq_a - Theta feo_a from the upstream
+// nodes and add Theta J(x) to the momentum (sum_a feo_a = 0,
+// sum_a c_a feo_a = J).  With feo_a = 3 w_a c_a.J and 3 (1 - Theta) = 18 nu,
+// g_a = h_a - w_a = w_a [dr + 18 nu c.J + 4.5 rho (c.u)^2 - 1.5 rho u^2],
+// rho u_i u_j = P_ij from the row's flux values:
+//   g1,3 = q + Pxx/2 +- tx,  g2,4 = q + Pyy/2 +- ty,  q = (dr - 1.5 (Pxx + Pyy)) / 9,
+//   g5,7 = d + Pxy/4 +- (sx + sy),  g6,8 = d - Pxy/4 +- (sy - sx),
+//   d = (dr + 3 (Pxx + Pyy)) / 36,  t = 2 nu J,  s = t / 4 (exact),
+//   g0 = dr - 2 (g-pairs' even parts), equal to 4 q, so that sum g = dr
+// without the bias of the rounded 1/9 and 1/36.  The momentum the node
+// sends out is 3 t; the close adds J - 3 t of the receiving node (Theta J),
+// so the lattice's momentum cancels term by term (see the close).
+__device__ __forceinline__ void reconstruct_lw2(float2 dr, float2 Jx, float2 Jy, float2 pxx,
+                                                float2 pxy, float2 pyy, const StreamCoeffs& k,
+                                                float2 g[9]) {
+    const float2 S = add2(pxx, pyy);
+    const float2 q = fma2(S, sp(-1.f / 6.f), mul2(dr, sp(1.f / 9.f)));
+    const float2 ax = fma2(pxx, sp(0.5f), q), ay = fma2(pyy, sp(0.5f), q);
+    const float2 d = fma2(S, sp(1.f / 12.f), mul2(dr, sp(1.f / 36.f)));
+    const float2 dp = fma2(pxy, sp(0.25f), d), dm = fma2(pxy, sp(-0.25f), d);
+    const float2 tx = mul2(Jx, sp(k.lw_t)), ty = mul2(Jy, sp(k.lw_t));
+    const float2 sx = mul2(Jx, sp(k.lw_s)), sy = mul2(Jy, sp(k.lw_s));
+    const float2 spp = add2(sx, sy), smm = sub2(sy, sx);
+    g[0] = fma2(sp(-2.f), add2(add2(ax, ay), add2(dp, dm)), dr);
     g[1] = add2(ax, tx);
     g[3] = sub2(ax, tx);
     g[2] = add2(ay, ty);

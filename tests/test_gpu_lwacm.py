@@ -1,0 +1,132 @@
+"""LW-ACM (Sec. 1-b, Eq. 3) on the GPU against the FP64 oracle, element by
+element on the same seeded inputs: the radius-0 instance of the streaming
+kernel (no finite differences; the equilibria minus Theta times their odd
+part gathered from the upstream nodes, plus Theta J at the node).
+
+Tolerance (FP32 storage and arithmetic): 1e-5 of the velocity amplitude of
+the initial field, as for the other schemes."""
+import numpy as np
+import pytest
+
+from paper_1803_00437_gb300 import inputs
+from parity_util import amplitude, as_f32, gpu_run, max_err, oracle_run
+
+pytestmark = pytest.mark.gpu
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1803_00437_gb300 import build
+    build.build()
+
+
+def _cfg(nx, ny, nu, **kw):
+    from paper_1803_00437_gb300 import fdlbm as F
+    return F.LatticeConfig(nx, ny, "lwacm", s_xx=F.nu_to_s(nu), **kw)
+
+
+@pytest.mark.parametrize("shape", [(256, 64), (264, 40), (512, 37), (384, 100), (1024, 16)])
+def test_lwacm_parity(oracle, shape):
+    """Several strips and row segments, a partial last strip (264), odd
+    heights; 32 seeded modes plus density noise, 300 steps."""
+    nx, ny = shape
+    modes = inputs.random_modes(nx, ny, 32, 2e-3, seed=nx + 3 * ny)
+    d, ux, uy = inputs.transverse_modes(nx, ny, modes)
+    d = inputs.random_fields(nx, ny, 0.0, seed=4, rho_amp=1e-3)[0]
+    f = as_f32((d, ux, uy))
+    cfg = _cfg(nx, ny, 0.02)
+    gpu, _ = gpu_run(cfg, f, 300)
+    ref = oracle_run(oracle, cfg, f, 300)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+def test_lwacm_shear_wave_with_mean_flow(oracle):
+    """The Fig. 1 set-up at a GPU-supported size: a shear wave carried by a
+    mean velocity along k (256 x 256, k = (3, 2) 2 pi / 256, V = 0.05),
+    1000 steps."""
+    N, A, V = 256, 1e-3, 0.05
+    kx, ky = 2 * np.pi * 3 / N, 2 * np.pi * 2 / N
+    k = np.hypot(kx, ky)
+    X, Y = np.meshgrid(np.arange(N), np.arange(N))
+    ph = kx * X + ky * Y
+    ux = -A * ky / k * np.cos(ph) + kx / k * V
+    uy = A * kx / k * np.cos(ph) + ky / k * V
+    f = as_f32((np.zeros((N, N)), ux, uy))
+    cfg = _cfg(N, N, 0.01)
+    gpu, _ = gpu_run(cfg, f, 1000)
+    ref = oracle_run(oracle, cfg, f, 1000)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32  # amplitude includes V
+
+
+def test_lwacm_fp16_storage_close_to_fp32():
+    nx, ny = 512, 128
+    f = as_f32(inputs.random_fields(nx, ny, 0.01, seed=9, rho_amp=0.002))
+    a, _ = gpu_run(_cfg(nx, ny, 0.03), f, 200)
+    b, _ = gpu_run(_cfg(nx, ny, 0.03, storage="f16"), f, 200)
+    assert max_err(a, b, amplitude(f)) <= 2e-2
+
+
+def test_lwacm_conserves_mass_and_momentum_without_bias():
+    """Uniform offsets rho - 1 = 0.01 and u = (0.02, -0.01) under seeded noise,
+    512 x 128, 2000 steps.  A reconstruction that relies on a rounded
+    constant (1/9, 1/36, Theta) to balance the totals moves them by ~2^-24
+    of themselves every step; the unbiased forms leave only the rounding of
+    the gathered sums and of the stored fields, which on near-uniform
+    fields is correlated but far smaller.  Bound: 2^-27 of the total per
+    step (an eighth of that signature)."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    nx, ny, n = 512, 128, 2000
+    d, ux, uy = inputs.random_fields(nx, ny, 0.005, seed=11, rho_amp=0.002)
+    f = as_f32((d + 0.01, ux + 0.02, uy - 0.01))
+    lat = F.Lattice(_cfg(nx, ny, 0.03))
+    lat.init(*[torch.from_numpy(x).cuda() for x in f])
+    m0, p0 = lat.reduce("mass")[0], lat.reduce("momentum")
+    lat.step(n)
+    m1, p1 = lat.reduce("mass")[0], lat.reduce("momentum")
+    per_step = 2.0 ** -27 * n
+    print({"mass_drift_per_step_rel": abs(m1 - m0) / abs(m0) / n,
+           "momentum_drift_per_step_rel": (np.abs(p1 - p0) / np.abs(p0) / n).tolist()})
+    assert abs(m1 - m0) <= per_step * abs(m0), (m1 - m0, m0)
+    assert np.all(np.abs(p1 - p0) <= per_step * np.abs(p0)), (p1 - p0, p0)
+
+
+def test_lwacm_full_size_sampled_8192(oracle):
+    """8192 x 8192, 32 seeded modes of amplitude 1e-3, one step in the
+    benchmark's launch configuration, against the oracle's point-wise step
+    at 4096 sampled nodes plus the four edges."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    N = 8192
+    modes = inputs.random_modes(N, N, 32, 1e-3, seed=inputs.seed_for(1))
+    f = as_f32(inputs.transverse_modes(N, N, modes))
+    cfg = _cfg(N, N, 0.01)
+    lat = F.Lattice(cfg)
+    lat.init(*[torch.from_numpy(a).to(lat.device) for a in f])
+    lat.step(1)
+    out = [t.cpu().numpy() for t in lat.moments()]
+    lat.close()
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([rng.integers(0, N * N, 4096),
+                          [0, N - 1, N * (N - 1), N * N - 1]]).astype(np.int64)
+    from parity_util import oracle_params
+    p = oracle_params(oracle, cfg)
+    d, x, y = (a.astype(np.float64) for a in f)
+    ref = oracle.lwacm_step_points(p, 1.0 + d, x, y, idx)
+    A = amplitude(f)
+    assert np.abs(out[0].ravel()[idx] - (ref[:, 0] - 1.0)).max() <= TOL32 * A
+    assert np.abs(out[1].ravel()[idx] - ref[:, 1]).max() <= TOL32 * A
+    assert np.abs(out[2].ravel()[idx] - ref[:, 2]).max() <= TOL32 * A
+
+
+def test_lwacm_rejects_unsupported_lattices():
+    from paper_1803_00437_gb300 import fdlbm as F
+    for kw in (dict(nx=250, ny=64), dict(nx=256, ny=64, boundary="walls_y"),
+               dict(nx=256, ny=64, force=(1e-5, 0.0)), dict(nx=256, ny=64, flags=F.FLAG_TILED)):
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        with pytest.raises(F.FdlbmError):
+            F.Lattice(_cfg(nx, ny, 0.02, **kw))
