@@ -32,8 +32,8 @@ N_MODES = 32
 AMP = 1e-3
 NU = 0.01
 S_E = 1.5
-BYTES_PER_LUP = {"fd5": 24, "mrt": 72}  # read + write of the state per node update (FP32)
-WORKLOAD = (f"FD-LBM five-point and MRT D2Q9 side by side, {N_SIDE}x{N_SIDE} periodic, "
+BYTES_PER_LUP = {"fd5": 24, "mrt": 72, "lwacm": 24}  # read + write of the state per node update (FP32)
+WORKLOAD = (f"FD-LBM five-point and MRT D2Q9 (and LW-ACM) side by side, {N_SIDE}x{N_SIDE} periodic, "
             f"{N_MODES} seeded transverse modes A={AMP}, nu={NU}, s_e={S_E}, FP32")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -119,7 +119,8 @@ def hbm_peak():
 # The translation unit of each profiled kernel; its hash covers the unit and
 # every header it includes (transitively), so a recorded DRAM figure is used
 # only while that kernel's code is unchanged.
-KERNEL_UNITS = {"fd_step": "fd_step_stream.cu", "mrt_step": "mrt_step.cu"}
+KERNEL_UNITS = {"fd_step": "fd_step_stream.cu", "mrt_step": "mrt_step.cu",
+                "lwacm_step": "fd_step_stream.cu"}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -293,7 +294,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     modes = inputs.random_modes(side, side, N_MODES, AMP, seed=inputs.seed_for(1) + rank)
     lats = {}
-    for scheme in ("fd5", "mrt"):
+    for scheme in ("fd5", "mrt", "lwacm"):
         cfg = F.LatticeConfig(side, side, scheme, s_xx=s_xx, s_e=S_E)
         lat = F.Lattice(cfg, device=dev, stream=stream)
         lat.init_modes(modes)
@@ -365,18 +366,21 @@ def run_ours(args):
 
     value, fd_ms = job_mlups(nodes, results["fd5"]["ms"] / args.steps, world, dev)
     mrt_value, mrt_ms = job_mlups(nodes, results["mrt"]["ms"] / args.steps, world, dev)
+    lw_value, lw_ms = job_mlups(nodes, results["lwacm"]["ms"] / args.steps, world, dev)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(fd_ms, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": side, "ny": side, "scheme": "fd5",
-                   "l2": "state larger than L2 (805 MB FD-LBM, 2.4 GB MRT): no flush",
+                   "l2": "state larger than L2 (805 MB FD-LBM and LW-ACM, 2.4 GB MRT): no flush",
                    "parallelism": f"{world} independent lattice(s), one per GPU"},
         "roofline": roofline("fd5", "fd_step"),
         "mrt": {"value": round(mrt_value, 1), "unit": "MLUPS",
                 "ms_per_step": round(mrt_ms, 5), "roofline": roofline("mrt", "mrt_step")},
         "fd_over_mrt_speedup": round(mrt_ms / fd_ms, 3),
+        "lwacm": {"value": round(lw_value, 1), "unit": "MLUPS",
+                  "ms_per_step": round(lw_ms, 5), "roofline": roofline("lwacm", "lwacm_step")},
         "gpu_launches": int(sum(r["launches"] for r in results.values())),
         "clocks": clocks, "health": health, "e2e": e2e,
     }
