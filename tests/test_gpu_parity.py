@@ -161,6 +161,28 @@ def test_poiseuille_steady_state_256x64(oracle, scheme):
     assert abs(umg / (F * H * H / (8 * nu)) - 1) <= 0.02
 
 
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+def test_shear_wave_in_mean_flow(oracle, scheme):
+    """A shear wave carried by a mean flow V = 0.1 along an oblique k (the
+    Galilean set-up of Sec. 1-a / Sec. 2, where the nonlinear theta terms
+    and the equilibria's u u terms are of order V^2 = 1e-2, not A^2), 264 x 96
+    periodic, 500 steps; tolerance 1e-5 of the field amplitude (V + A)."""
+    nx, ny, A, V = 264, 96, 1e-3, 0.1
+    kx, ky = 2 * np.pi * 2 / nx, 2 * np.pi * 1 / ny
+    k = np.hypot(kx, ky)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ph = kx * X + ky * Y
+    ux = -A * ky / k * np.cos(ph) + kx / k * V
+    uy = A * kx / k * np.cos(ph) + ky / k * V
+    f = as_f32((np.zeros((ny, nx)), ux, uy))
+    from paper_1803_00437_gb300 import fdlbm as F
+    flags = 0 if scheme == "mrt" else F.FLAG_STREAM
+    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.02), s_e=1.5, flags=flags)
+    gpu, _ = gpu_run(cfg, f, 500)
+    ref = oracle_run(oracle, cfg, f, 500)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
 def test_zero_steps_returns_initial_state(oracle):
     f = as_f32(inputs.random_fields(24, 20, 0.02, seed=1, rho_amp=0.01))
     for scheme in ("fd3", "fd5"):
