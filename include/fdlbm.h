@@ -1,5 +1,5 @@
 /*
- * fdlbm.h -- C ABI of the GB300 (sm_103a) FD-LBM / MRT D2Q9 library.
+ * fdlbm.h -- C ABI of the GB300 (sm_103a) FD-LBM / MRT / LW-ACM D2Q9 library.
  *
  * The schemes are those of Dubois, Lallemand, Obrecht, Tekitek, "Lattice
  * Boltzmann model approximated with finite difference expressions"
@@ -12,6 +12,8 @@
  *     propagates them one link (Eq. 2).
  *   - MRT D2Q9 (Sec. 1, 1-a): collision of the non-conserved moments towards
  *     their equilibria (Eq. 1) and propagation (Eq. 2).
+ *   - LW-ACM (Sec. 1-b, Eq. 3): the same (rho, ux, uy) state, every link
+ *     rebuilt from equilibria alone (no finite differences) and propagated.
  *   - Body force: Strang splitting, half before and half after the
  *     collision (Sec. 1).  Walls (Sec. 3-b, 3-c): FD-LBM extrapolates the
  *     velocity linearly to zero at walls placed xi outside the first and
