@@ -116,9 +116,9 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# The translation unit of each profiled kernel; its hash covers the unit and
-# every header it includes (transitively), so a recorded DRAM figure is used
-# only while that kernel's code is unchanged.
+# The translation unit of each profiled kernel; its hash covers the code (not
+# the comments) of the unit and of every header it includes (transitively), so
+# a recorded DRAM figure is used only while that kernel's code is unchanged.
 KERNEL_UNITS = {"fd_step": "fd_step_stream.cu", "mrt_step": "mrt_step.cu",
                 "lwacm_step": "fd_step_stream.cu"}
 
@@ -144,10 +144,20 @@ def kernel_source_hash(kernel: str) -> str:
         for d in (csrc, inc):
             path = os.path.join(d, name)
             if os.path.exists(path):
-                with open(path, "rb") as fh:
-                    h.update(name.encode() + b"\0" + fh.read())
+                with open(path) as fh:
+                    code = _strip_comments(fh.read())
+                h.update(name.encode() + b"\0" + code.encode())
                 break
     return h.hexdigest()[:16]
+
+
+def _strip_comments(src: str) -> str:
+    """C/C++ source without comments and with whitespace collapsed, so that
+    only code changes alter a kernel's hash."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
 
 
 def recorded_traffic(kernel: str, nodes: int):
