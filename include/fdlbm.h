@@ -65,9 +65,9 @@ extern "C" {
 /* Link-wise artificial compressibility method (Sec. 1-b, Eq. 3): every link
  * rebuilt from equilibria alone, f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) -
  * feo_a(x - c_a)), feo the odd part of feq, Theta = 1 - 6 nu, nu from s_xx as
- * for the other schemes; s_e is not used.  Same (rho - 1, ux, uy) state and
- * storage options as FD-LBM.  Periodic lattices with nx % 8 == 0, nx >= 256,
- * ny >= 16, no force (FDLBM_ERR_UNSUPPORTED otherwise). */
+ * for the other schemes; s_e is not used.  Same (rho - 1, ux, uy) state,
+ * storage options and kernel choice (FDLBM_FLAG_*) as FD-LBM.  Periodic
+ * lattices without force (FDLBM_ERR_UNSUPPORTED otherwise). */
 #define FDLBM_SCHEME_LWACM 200
 
 #define FDLBM_BOUNDARY_PERIODIC 0 /* periodic in x and y                  */

@@ -1,6 +1,8 @@
 // fd_step_tiled.cu -- general FD-LBM step kernel (Sec. 2, Eq. 2): 2-D tiles
 // staged in shared memory with a halo of r + 1 nodes.  Handles periodic and
 // channel (walls in y) lattices of any size and FP32 / FP16 / BF16 storage.
+// Stencil radius r = 0 is LW-ACM (Sec. 1-b, Eq. 3): no finite differences,
+// a one-node halo for the gather.
 //
 // Per CTA (TX x TY outputs):
 //   1. load (rho-1, u) of the tile plus a halo of H = r + 1 nodes (gradients
@@ -18,10 +20,35 @@ namespace {
 
 constexpr int kTX = 32, kTY = 16, kThreads = 256;
 
+// LW-ACM populations g_a = h_a - w_a, h_a = feq_a - Theta feo_a, of one node
+// (Sec. 1-b, Eq. 3), with 3 (1 - Theta) = 18 nu and t = 2 nu J:
+//   g1,3 = q + Pxx/2 +- tx, g2,4 = q + Pyy/2 +- ty, q = (dr - 1.5 (Pxx + Pyy)) / 9,
+//   g5,7 = d + Pxy/4 +- (tx + ty)/4, g6,8 = d - Pxy/4 +- (ty - tx)/4,
+//   d = (dr + 3 (Pxx + Pyy)) / 36, g0 = dr - 2 (even parts)  (sum g = dr).
+__device__ __forceinline__ void lw_reconstruct(float dr, float Jx, float Jy, float pxx,
+                                               float pxy, float pyy, float lw_t, float g[9]) {
+    const float S = pxx + pyy;
+    const float q = fmaf(S, -1.f / 6.f, dr * (1.f / 9.f));
+    const float ax = fmaf(pxx, 0.5f, q), ay = fmaf(pyy, 0.5f, q);
+    const float d = fmaf(S, 1.f / 12.f, dr * (1.f / 36.f));
+    const float dp = fmaf(pxy, 0.25f, d), dm = fmaf(pxy, -0.25f, d);
+    const float tx = Jx * lw_t, ty = Jy * lw_t;
+    const float spp = 0.25f * tx + 0.25f * ty, smm = 0.25f * ty - 0.25f * tx;
+    g[0] = fmaf(-2.f, (ax + ay) + (dp + dm), dr);
+    g[1] = ax + tx;
+    g[3] = ax - tx;
+    g[2] = ay + ty;
+    g[4] = ay - ty;
+    g[5] = dp + spp;
+    g[7] = dp - spp;
+    g[6] = dm + smm;
+    g[8] = dm - smm;
+}
+
 template <int R, bool WALLS, typename T>
 __global__ void __launch_bounds__(kThreads)
     fd_step_tiled_kernel(FdState<T> src, FdState<T> dst, int nx, int ny, size_t pitch,
-                         FdCoeffs c) {
+                         FdCoeffs c, float lw_t) {
     constexpr int H = R + 1;
     constexpr int LX = kTX + 2 * H, LY = kTY + 2 * H, LN = LX * LY;
     constexpr int GX = kTX + 2, GY = kTY + 2, GN = GX * GY;
@@ -52,6 +79,13 @@ __global__ void __launch_bounds__(kThreads)
     for (int t = threadIdx.x; t < GN; t += kThreads) {
         const int gx = t % GX, gy = t / GX;
         const int l = (gy + H - 1) * LX + (gx + H - 1);
+        float g[9];
+        if (R == 0) {
+            lw_reconstruct(sf[0][l], sf[3][l], sf[4][l], sf[5][l], sf[6][l], sf[7][l], lw_t, g);
+#pragma unroll
+            for (int a = 0; a < 9; ++a) sg[a][t] = g[a];
+            continue;
+        }
         NodeDerivs d;
         d.drx = fd_deriv<R>(&sf[0][l], 1);
         d.dry = fd_deriv<R>(&sf[0][l], LX);
@@ -63,7 +97,6 @@ __global__ void __launch_bounds__(kThreads)
         d.dPxy_x = fd_deriv<R>(&sf[6][l], 1);
         d.dPxy_y = fd_deriv<R>(&sf[6][l], LX);
         d.dPyy_y = fd_deriv<R>(&sf[7][l], LX);
-        float g[9];
         fd_reconstruct(sf[0][l], sf[1][l], sf[2][l], d, c, g);
 #pragma unroll
         for (int a = 0; a < 9; ++a) sg[a][t] = g[a];
@@ -86,7 +119,23 @@ __global__ void __launch_bounds__(kThreads)
         p[7] = sg[7][b + GX + 1];   // from (x+1, y+1)
         p[8] = sg[8][b + GX - 1];   // from (x-1, y+1)
         float dr, ux, uy;
-        fd_close(p, c, &dr, &ux, &uy);
+        if (R == 0) {
+            // LW-ACM: Theta J of the node added as J - 3 t, t = 2 nu J the
+            // product this node sent to its neighbours (no bias in the totals)
+            const int l = (oy + H) * LX + (ox + H);
+            const float Jx = sf[3][l], Jy = sf[4][l];
+            const float drn =
+                p[0] + (p[1] + p[3]) + (p[2] + p[4]) + (p[5] + p[7]) + (p[6] + p[8]);
+            const float d57 = p[5] - p[7], d86 = p[8] - p[6];
+            const float px = ((p[1] - p[3]) + d57 + d86) + fmaf(-3.f, Jx * lw_t, Jx);
+            const float py = ((p[2] - p[4]) + d57 - d86) + fmaf(-3.f, Jy * lw_t, Jy);
+            const float inv = __frcp_rn(1.f + drn);
+            dr = drn;
+            ux = fmaf(-px * drn, inv, px);
+            uy = fmaf(-py * drn, inv, py);
+        } else {
+            fd_close(p, c, &dr, &ux, &uy);
+        }
         const size_t o = (size_t)y * pitch + x;
         Storage<T>::store(dst.drho + o, dr);
         Storage<T>::store(dst.ux + o, ux);
@@ -107,9 +156,10 @@ cudaError_t launch_typed(fdlbm_s* h, const void* src, void* dst) {
     c.fx = (float)h->p.force_x;
     c.fy = (float)h->p.force_y;
     c.xi = (float)h->p.wall_xi;
+    const float lw_t = (float)(2.0 * (1.0 / h->p.s_xx - 0.5) / 3.0);  // LW-ACM: 2 nu
     dim3 grid((h->p.nx + kTX - 1) / kTX, (h->p.ny + kTY - 1) / kTY);
     fd_step_tiled_kernel<R, WALLS, T>
-        <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c);
+        <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c, lw_t);
     return cudaGetLastError();
 }
 
@@ -121,6 +171,7 @@ cudaError_t launch_boundary(fdlbm_s* h, const void* src, void* dst) {
 
 template <typename T>
 cudaError_t launch_stencil(fdlbm_s* h, const void* src, void* dst) {
+    if (h->p.scheme == FDLBM_SCHEME_LWACM) return launch_typed<0, false, T>(h, src, dst);
     if (h->p.scheme == FDLBM_SCHEME_FD3) return launch_boundary<1, T>(h, src, dst);
     return launch_boundary<2, T>(h, src, dst);
 }

@@ -74,14 +74,9 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     }
     if (!(p->force_x == p->force_x) || !(p->force_y == p->force_y))
         return fail(FDLBM_ERR_INVALID, "force is NaN");
-    if (p->scheme == FDLBM_SCHEME_LWACM) {
-        if (p->boundary != FDLBM_BOUNDARY_PERIODIC || p->force_x != 0.0 || p->force_y != 0.0)
-            return fail(FDLBM_ERR_UNSUPPORTED, "LWACM: periodic lattices without force only");
-        if (p->flags & FDLBM_FLAG_TILED)
-            return fail(FDLBM_ERR_UNSUPPORTED, "LWACM runs on the streaming kernel only");
-        if (!fdlbm::fd_stream_supported(*p))
-            return fail(FDLBM_ERR_UNSUPPORTED, "LWACM needs nx % 8 == 0, nx >= 256, ny >= 16");
-    }
+    if (p->scheme == FDLBM_SCHEME_LWACM &&
+        (p->boundary != FDLBM_BOUNDARY_PERIODIC || p->force_x != 0.0 || p->force_y != 0.0))
+        return fail(FDLBM_ERR_UNSUPPORTED, "LWACM: periodic lattices without force only");
     return FDLBM_OK;
 }
 
@@ -449,8 +444,7 @@ cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
     // the streaming kernel pays off once the lattice fills the GPU's warps
     constexpr int64_t kStreamMinNodes = 1 << 20;
     const bool big = (int64_t)h->p.nx * h->p.ny >= kStreamMinNodes;
-    const bool lw = h->p.scheme == FDLBM_SCHEME_LWACM;  // streaming kernel only
-    if (h->fd_path != 1 && fd_stream_supported(h->p) && (big || lw || h->fd_path == 2))
+    if (h->fd_path != 1 && fd_stream_supported(h->p) && (big || h->fd_path == 2))
         return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }

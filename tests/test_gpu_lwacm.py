@@ -1,7 +1,8 @@
 """LW-ACM (Sec. 1-b, Eq. 3) on the GPU against the FP64 oracle, element by
-element on the same seeded inputs: the radius-0 instance of the streaming
-kernel (no finite differences; the equilibria minus Theta times their odd
-part gathered from the upstream nodes, plus Theta J at the node).
+element on the same seeded inputs: the radius-0 instances of the streaming
+and the tiled kernels (no finite differences; the equilibria minus Theta
+times their odd part gathered from the upstream nodes, plus Theta J at the
+node).
 
 Tolerance (FP32 storage and arithmetic): 1e-5 of the velocity amplitude of
 the initial field, as for the other schemes."""
@@ -38,14 +39,40 @@ def test_lwacm_parity(oracle, shape):
     d, ux, uy = inputs.transverse_modes(nx, ny, modes)
     d = inputs.random_fields(nx, ny, 0.0, seed=4, rho_amp=1e-3)[0]
     f = as_f32((d, ux, uy))
+    from paper_1803_00437_gb300 import fdlbm as F
+    cfg = _cfg(nx, ny, 0.02, flags=F.FLAG_STREAM)
+    gpu, _ = gpu_run(cfg, f, 300)
+    ref = oracle_run(oracle, cfg, f, 300)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
+@pytest.mark.parametrize("shape", [(191, 191), (64, 48), (100, 37), (33, 17)])
+def test_lwacm_tiled_parity(oracle, shape):
+    """Lattices of any size take the tiled kernel (odd sizes, partial tiles,
+    the 191 x 191 lattice of Fig. 1); seeded modes plus density noise, 300
+    steps."""
+    nx, ny = shape
+    modes = inputs.random_modes(nx, ny, 8, 2e-3, seed=nx * 5 + ny)
+    d, ux, uy = inputs.transverse_modes(nx, ny, modes)
+    d = inputs.random_fields(nx, ny, 0.0, seed=8, rho_amp=1e-3)[0]
+    f = as_f32((d, ux, uy))
     cfg = _cfg(nx, ny, 0.02)
     gpu, _ = gpu_run(cfg, f, 300)
     ref = oracle_run(oracle, cfg, f, 300)
     assert max_err(gpu, ref, amplitude(f)) <= TOL32
 
 
+def test_lwacm_streaming_equals_tiled():
+    from paper_1803_00437_gb300 import fdlbm as F
+    nx, ny = 392, 72
+    f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=8, rho_amp=0.005))
+    a, _ = gpu_run(_cfg(nx, ny, 0.03, flags=F.FLAG_STREAM), f, 50)
+    b, _ = gpu_run(_cfg(nx, ny, 0.03, flags=F.FLAG_TILED), f, 50)
+    assert max_err(a, b, amplitude(f)) <= TOL32
+
+
 def test_lwacm_shear_wave_with_mean_flow(oracle):
-    """The Fig. 1 set-up at a GPU-supported size: a shear wave carried by a
+    """The Fig. 1 set-up on the streaming kernel: a shear wave carried by a
     mean velocity along k (256 x 256, k = (3, 2) 2 pi / 256, V = 0.05),
     1000 steps."""
     N, A, V = 256, 1e-3, 0.05
@@ -65,8 +92,9 @@ def test_lwacm_shear_wave_with_mean_flow(oracle):
 def test_lwacm_fp16_storage_close_to_fp32():
     nx, ny = 512, 128
     f = as_f32(inputs.random_fields(nx, ny, 0.01, seed=9, rho_amp=0.002))
-    a, _ = gpu_run(_cfg(nx, ny, 0.03), f, 200)
-    b, _ = gpu_run(_cfg(nx, ny, 0.03, storage="f16"), f, 200)
+    from paper_1803_00437_gb300 import fdlbm as F
+    a, _ = gpu_run(_cfg(nx, ny, 0.03, flags=F.FLAG_STREAM), f, 200)
+    b, _ = gpu_run(_cfg(nx, ny, 0.03, storage="f16", flags=F.FLAG_STREAM), f, 200)
     assert max_err(a, b, amplitude(f)) <= 2e-2
 
 
@@ -125,16 +153,16 @@ def test_lwacm_full_size_sampled_8192(oracle):
 
 def test_lwacm_rejects_unsupported_lattices():
     from paper_1803_00437_gb300 import fdlbm as F
-    for kw in (dict(nx=250, ny=64), dict(nx=256, ny=64, boundary="walls_y"),
-               dict(nx=256, ny=64, force=(1e-5, 0.0)), dict(nx=256, ny=64, flags=F.FLAG_TILED)):
+    for kw in (dict(nx=256, ny=64, boundary="walls_y"), dict(nx=250, ny=64, force=(1e-5, 0.0))):
         nx, ny = kw.pop("nx"), kw.pop("ny")
         with pytest.raises(F.FdlbmError):
             F.Lattice(_cfg(nx, ny, 0.02, **kw))
 
 
 def test_fig1_damping_vs_mean_velocity_on_the_gpu():
-    """The comparison of Fig. 1 and Sec. 1-b on the GPU path: a shear wave
-    of wave vector (3, 2) 2 pi / 256 carried by a mean velocity V along k,
+    """The comparison of Fig. 1 and Sec. 1-b on the GPU path, on the lattice
+    of Fig. 1: 191 x 191, shear wave of wave vector (3, 2) 2 pi / 191 carried
+    by a mean velocity V along k,
     nu = 0.01, 600 steps, rates from the device's FP64 mode projections.
     LW-ACM damps at (nu - V^2/2) k^2 (half the rate at V = 0.1); FD-LBM five
     points at nu (1 - 3 V^2) k^2 (the D2Q9 Galilean defect, 3 % at V = 0.1).
@@ -142,7 +170,7 @@ def test_fig1_damping_vs_mean_velocity_on_the_gpu():
     import json
     import torch
     from paper_1803_00437_gb300 import fdlbm as F
-    N, A, nu, steps = 256, 1e-4, 0.01, 600
+    N, A, nu, steps = 191, 1e-4, 0.01, 600
     m, n = 3, 2
     kx, ky = 2 * np.pi * m / N, 2 * np.pi * n / N
     k = np.hypot(kx, ky)
@@ -154,8 +182,7 @@ def test_fig1_damping_vs_mean_velocity_on_the_gpu():
             ux = -A * ky / k * np.cos(ph) + kx / k * V
             uy = A * kx / k * np.cos(ph) + ky / k * V
             f = as_f32((np.zeros((N, N)), ux, uy))
-            cfg = F.LatticeConfig(N, N, scheme, s_xx=F.nu_to_s(nu), s_e=1.5,
-                                  flags=F.FLAG_STREAM)
+            cfg = F.LatticeConfig(N, N, scheme, s_xx=F.nu_to_s(nu), s_e=1.5)
             lat = F.Lattice(cfg)
             lat.init(*[torch.from_numpy(a).cuda() for a in f])
             a0 = complex(*lat.reduce("mode", (m, n)))
