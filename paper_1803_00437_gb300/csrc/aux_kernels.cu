@@ -102,22 +102,58 @@ struct ModeList {
     double rec[kMaxModes][4];  // m, n, amplitude, phase
 };
 
-__global__ void modes_kernel(ModeList ml, int nx, int ny, float* __restrict__ drho,
-                             float* __restrict__ ux, float* __restrict__ uy) {
-    const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
+// Rows per block.  A cos(kx x + ky y + phase) = cos(kx x) C(y) - sin(kx x) S(y)
+// with C, S = A (cos, sin)(ky y + phase): the row factors of the block's rows
+// are tabulated once per block in shared memory (FP64 sincos of each row),
+// the column factor once per thread and mode, so each node costs four FP64
+// multiply-adds per mode instead of a sincos.
+constexpr int kModeRows = 16;
+
+__global__ void __launch_bounds__(kThreads)
+    modes_kernel(ModeList ml, int nx, int ny, float* __restrict__ drho, float* __restrict__ ux,
+                 float* __restrict__ uy) {
+    __shared__ double2 rowf[kMaxModes][kModeRows];
+    const int x = blockIdx.x * kThreads + threadIdx.x;
+    const int y0 = blockIdx.y * kModeRows;
+    const int nrows = min(kModeRows, ny - y0);
+    for (int t = threadIdx.x; t < ml.n * kModeRows; t += kThreads) {
+        const int k = t / kModeRows, r = t % kModeRows;
+        const double ky = 2.0 * M_PI * ml.rec[k][1] / ny;
+        double sn, cs;
+        sincos(ky * (double)(y0 + r) + ml.rec[k][3], &sn, &cs);
+        rowf[k][r] = make_double2(ml.rec[k][2] * cs, ml.rec[k][2] * sn);
+    }
+    __syncthreads();
     if (x >= nx) return;
-    double vx = ml.mean_ux, vy = ml.mean_uy;
+    double vx[kModeRows], vy[kModeRows];
+#pragma unroll
+    for (int r = 0; r < kModeRows; ++r) {
+        vx[r] = ml.mean_ux;
+        vy[r] = ml.mean_uy;
+    }
     for (int k = 0; k < ml.n; ++k) {
         const double kx = 2.0 * M_PI * ml.rec[k][0] / nx, ky = 2.0 * M_PI * ml.rec[k][1] / ny;
         const double kk = sqrt(kx * kx + ky * ky);
-        const double w = ml.rec[k][2] * cos(kx * x + ky * y + ml.rec[k][3]);
-        vx += -w * ky / kk;
-        vy += w * kx / kk;
+        const double tx = -ky / kk, ty = kx / kk;  // unit vector across k
+        double sx, cx;
+        sincos(kx * (double)x, &sx, &cx);
+#pragma unroll
+        for (int r = 0; r < kModeRows; ++r) {
+            const double2 f = rowf[k][r];
+            const double w = fma(cx, f.x, -sx * f.y);
+            vx[r] = fma(w, tx, vx[r]);
+            vy[r] = fma(w, ty, vy[r]);
+        }
     }
-    const size_t i = (size_t)y * nx + x;
-    drho[i] = 0.f;
-    ux[i] = (float)vx;
-    uy[i] = (float)vy;
+#pragma unroll
+    for (int r = 0; r < kModeRows; ++r) {
+        if (r < nrows) {
+            const size_t i = (size_t)(y0 + r) * nx + x;
+            drho[i] = 0.f;
+            ux[i] = (float)vx[r];
+            uy[i] = (float)vy[r];
+        }
+    }
 }
 
 // ---- moments ---------------------------------------------------------------------
@@ -438,7 +474,7 @@ cudaError_t launch_modes_eval(fdlbm_s* h, int n_modes, const double* modes_host,
     ml.mean_uy = mean_uy;
     for (int k = 0; k < n_modes; ++k)
         for (int j = 0; j < 4; ++j) ml.rec[k][j] = modes_host[4 * k + j];
-    dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
+    dim3 grid((h->p.nx + kThreads - 1) / kThreads, (h->p.ny + kModeRows - 1) / kModeRows);
     modes_kernel<<<grid, kThreads, 0, h->stream>>>(ml, h->p.nx, h->p.ny, drho, ux, uy);
     return cudaGetLastError();
 }
