@@ -170,28 +170,12 @@ struct RowStep {
                 nuy[1] = mul2(nuy[1], fac);
             }
         }
-        Win nw;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 jx = fma2(nr[h], nux[h], nux[h]), jy = fma2(nr[h], nuy[h], nuy[h]);
-            nw.v[W_R][h] = nr[h];
-            nw.v[W_JX][h] = jx;
-            nw.v[W_JY][h] = jy;
-            nw.v[W_PXY][h] = mul2(jx, nuy[h]);
-            nw.v[W_PYY][h] = mul2(jy, nuy[h]);
-        }
         // centre row c = r - R from its ring slot (still resident); before
         // the window is full the centre row does not exist yet
         const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
-        if (R == 0) {  // LW-ACM: no derivative window, the new row is the centre
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                cux[h] = nux[h];
-                cuy[h] = nuy[h];
-            }
-        } else if (!WARM || k >= R) {
+        if (R > 0 && (!WARM || k >= R)) {
             if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
             Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
             Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
@@ -206,137 +190,9 @@ struct RowStep {
                 }
             }
         }
-        // Five points: the centre row's fields are rebuilt from the ring
-        // (only the differences are held in registers).  Three points: the
-        // centre row is held (fm1).
-        Win rebuilt;
-        if (R == 2) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 jx = fma2(cdr[h], cux[h], cux[h]), jy = fma2(cdr[h], cuy[h], cuy[h]);
-                rebuilt.v[W_R][h] = cdr[h];
-                rebuilt.v[W_JX][h] = jx;
-                rebuilt.v[W_JY][h] = jy;
-                rebuilt.v[W_PXY][h] = mul2(jx, cuy[h]);
-                rebuilt.v[W_PYY][h] = mul2(jy, cuy[h]);
-            }
-        }
-        const Win& cen = (R == 0) ? nw : (R == 1) ? fm1 : rebuilt;
-        // y derivatives at the centre row (scaled by 2 or 8):
-        //   three points: 2 d/dy = f(c+1) - f(c-1)
-        //   five points:  8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), d1(c+1) = f(r) - f(c);
-        //   the window holds n1 = -d1, so 8 d/dy = (-6 n1(c) + n1(c-1)) + n1(c+1);
-        //   the bracket does not wait for the new row
-        Win dy, d1new;
-#pragma unroll
-        for (int f = 0; f < W_N; ++f)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (R == 0) {
-                    dy.v[f][h] = sp(0.f);  // unused
-                } else if (R == 1) {
-                    dy.v[f][h] = sub2(nw.v[f][h], fm2.v[f][h]);
-                } else {
-                    d1new.v[f][h] = sub2(cen.v[f][h], nw.v[f][h]);
-                    dy.v[f][h] = add2(fma2(sp(-6.f), dm2.v[f][h], dm3.v[f][h]), d1new.v[f][h]);
-                }
-            }
-        // x derivatives at the centre row
-        float2 pxx[2], dxr[2], dxjx[2], dxjy[2], dxpxx[2], dxpxy[2];
-        pxx[0] = mul2(cen.v[W_JX][0], cux[0]);
-        pxx[1] = mul2(cen.v[W_JX][1], cux[1]);
-        float2 g[2][9];
-        if (R == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                reconstruct_lw2(cen.v[W_R][h], cen.v[W_JX][h], cen.v[W_JY][h], pxx[h],
-                                cen.v[W_PXY][h], cen.v[W_PYY][h], a.k, g[h]);
-        } else {
-            deriv_x<R>(cen.v[W_R], dxr);
-            deriv_x<R>(cen.v[W_JX], dxjx);
-            deriv_x<R>(cen.v[W_JY], dxjy);
-            deriv_x<R>(pxx, dxpxx);
-            deriv_x<R>(cen.v[W_PXY], dxpxy);
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                reconstruct2<FORCE>(cen.v[W_R][h], cux[h], cuy[h], cen.v[W_JX][h], cen.v[W_JY][h],
-                                pxx[h], cen.v[W_PXY][h], cen.v[W_PYY][h], dxr[h], dy.v[W_R][h], dxjx[h], dy.v[W_JX][h], dxjy[h],
-                                dy.v[W_JY][h], dxpxx[h], dxpxy[h], dy.v[W_PXY][h],
-                                dy.v[W_PYY][h], a.k, g[h]);
-        }
-
-        // populations crossing lane boundaries: right-going (1, 5, 8) of
-        // column 3 to the next lane, left-going (3, 6, 7) of column 0 back
-        const float in1 = __shfl_up_sync(kFull, g[1][1].y, 1);
-        const float in5 = __shfl_up_sync(kFull, g[1][5].y, 1);
-        const float in8 = __shfl_up_sync(kFull, g[1][8].y, 1);
-        const float in3 = __shfl_down_sync(kFull, g[0][3].x, 1);
-        const float in6 = __shfl_down_sync(kFull, g[0][6].x, 1);
-        const float in7 = __shfl_down_sync(kFull, g[0][7].x, 1);
-        // per destination column j (0..3): from j - 1 (1, 5, 8) and j + 1
-        // (3, 6, 7), summed in scalar FP32 (the results land in column pairs
-        // without register moves)
-        float G[9][4];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            G[q][0] = g[0][q].x;
-            G[q][1] = g[0][q].y;
-            G[q][2] = g[1][q].x;
-            G[q][3] = g[1][q].y;
-        }
-        float ss_[4], ds_[4], su_[4], du_[4], sd_[4], dd_[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float q1 = j ? G[1][j - 1] : in1, q5 = j ? G[5][j - 1] : in5;
-            const float q8 = j ? G[8][j - 1] : in8;
-            const float q3 = j < 3 ? G[3][j + 1] : in3, q6 = j < 3 ? G[6][j + 1] : in6;
-            const float q7 = j < 3 ? G[7][j + 1] : in7;
-            ss_[j] = G[0][j] + (q1 + q3);
-            ds_[j] = q1 - q3;
-            su_[j] = G[2][j] + (q5 + q6);
-            du_[j] = q5 - q6;
-            sd_[j] = G[4][j] + (q7 + q8);
-            dd_[j] = q8 - q7;
-        }
-
         float2 odr[2], oux[2], ouy[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float2 ss = make_float2(ss_[2 * h], ss_[2 * h + 1]);
-            const float2 ds = make_float2(ds_[2 * h], ds_[2 * h + 1]);
-            const float2 su = make_float2(su_[2 * h], su_[2 * h + 1]);
-            const float2 du = make_float2(du_[2 * h], du_[2 * h + 1]);
-            const float2 sd = make_float2(sd_[2 * h], sd_[2 * h + 1]);
-            const float2 dd = make_float2(dd_[2 * h], dd_[2 * h + 1]);
-            // close row c - 1: u = J - J dr / (1 + dr)
-            const float2 drn = add2(acc.ar[h], sd);
-            float2 px = add2(acc.ax[h], dd);
-            float2 py = sub2(acc.ay[h], sd);
-            if (FORCE) {
-                px = add2(px, sp(a.k.hfx));
-                py = add2(py, sp(a.k.hfy));
-            }
-            if (R == 0) {
-                // LW-ACM: Theta J = J - 3 t of the closing row (the previous
-                // row), t = 2 nu J the same product that row sent to its
-                // neighbours, so the momentum leaving and entering cancel
-                const float2 tx = mul2(fm1.v[W_JX][h], sp(a.k.lw_t));
-                const float2 ty = mul2(fm1.v[W_JY][h], sp(a.k.lw_t));
-                px = add2(px, fma2(sp(-3.f), tx, fm1.v[W_JX][h]));
-                py = add2(py, fma2(sp(-3.f), ty, fm1.v[W_JY][h]));
-            }
-            const float2 nrho = fma2(drn, sp(-1.f), sp(-1.f));  // -(1 + dr)
-            const float2 ninv = make_float2(rcp_approx(nrho.x), rcp_approx(nrho.y));
-            odr[h] = drn;
-            oux[h] = fma2(mul2(px, drn), ninv, px);
-            ouy[h] = fma2(mul2(py, drn), ninv, py);
-            // row c: upward part of row c - 1 plus the same-row part
-            acc.ar[h] = add2(acc.us[h], ss);
-            acc.ax[h] = add2(acc.ud[h], ds);
-            acc.ay[h] = acc.us[h];
-            acc.us[h] = su;
-            acc.ud[h] = du;
-        }
+        stream_row<R, FORCE>(nr, nux, nuy, cdr, cux, cuy, a.k, fm2, fm1, dm3, dm2, acc, odr, oux,
+                             ouy);
         // destination row c - 1 = yb + k - 2R - 2 is an output row from k = 2R + 2
         if ((!WARM || k >= warm_rows<R>()) && it.lane_stores) {
             T* dst = static_cast<T*>(a.dst) + it.out + (size_t)(k - 2 * R - 2) * a.pitch;
@@ -344,9 +200,6 @@ struct RowStep {
             Vec4<T>::store(dst + a.plane, oux);
             Vec4<T>::store(dst + 2 * a.plane, ouy);
         }
-        // rotate the window: the oldest row/difference take the new ones
-        if (R <= 1) fm2 = nw;
-        if (R == 2) dm3 = d1new;
     }
 };
 
