@@ -183,6 +183,27 @@ def test_shear_wave_in_mean_flow(oracle, scheme):
     assert max_err(gpu, ref, amplitude(f)) <= TOL32
 
 
+@pytest.mark.parametrize("scheme", ["fd3", "fd5", "mrt"])
+def test_sound_wave_in_mean_flow(oracle, scheme):
+    """A density wave in a mean flow V = 0.1 along an oblique k: it splits
+    into the up- and downstream sound waves whose damping depends on the
+    v^2 and v.grad(rho) terms of theta_E and theta_XX (Sec. 2), which no
+    state at rest exercises.  264 x 96 periodic, s_e = 1.8, 500 steps;
+    tolerance 1e-5 of the field amplitude (V + A)."""
+    nx, ny, A, V = 264, 96, 1e-3, 0.1
+    kx, ky = 2 * np.pi * 2 / nx, 2 * np.pi * 1 / ny
+    k = np.hypot(kx, ky)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ph = kx * X + ky * Y
+    f = as_f32((A * np.cos(ph), np.full((ny, nx), kx / k * V), np.full((ny, nx), ky / k * V)))
+    from paper_1803_00437_gb300 import fdlbm as F
+    flags = 0 if scheme == "mrt" else F.FLAG_STREAM
+    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.02), s_e=1.8, flags=flags)
+    gpu, _ = gpu_run(cfg, f, 500)
+    ref = oracle_run(oracle, cfg, f, 500)
+    assert max_err(gpu, ref, amplitude(f)) <= TOL32
+
+
 def test_zero_steps_returns_initial_state(oracle):
     f = as_f32(inputs.random_fields(24, 20, 0.02, seed=1, rho_amp=0.01))
     for scheme in ("fd3", "fd5"):

@@ -230,6 +230,83 @@ def test_sound_waves_in_mean_flow(oracle, stencil):
             assert abs(gm - gp) / g0 < 2.0 * V * V, (V, gm, gp)
 
 
+def sound_rates_in_mean_flow(nu, s_e, V, s_xx=None, printed_theta=True):
+    """Long-wave damping rates (upstream, downstream) of the two sound waves
+    of a 1-D lattice carrying a uniform V along the wave vector, derived by
+    hand from Eq. theta and the Remark of Sec. 2 (no oracle code involved).
+
+    Linearised about rho = 1, J = (V, 0), Eq. theta evaluated in full with
+    the Euler equations for d_t gives
+        theta_E  = 2 (1 - 9/2 V^2) dJ - 2 V (1 - 3 V^2) drho,
+        theta_XX = 2/3 (1 - 9/2 V^2) dJ - 2/3 V (1 - 3 V^2) drho
+    (E has zero flux at equilibrium since q = -J).  The momentum flux is
+    2 rho/3 + E/6 + XX/2 (rows of M), so the viscous flux of the Remark,
+    sigma_l Lambda theta_l, is D dJ - E' drho with D = (nu + zeta)(1 - 9/2 V^2)
+    and E' = (nu + zeta) V (1 - 3 V^2).  That is the MRT step.  The printed
+    theta of Sec. 2 (read on J, as the oracle does) differs from it by
+        d theta_E = 15 V^2 dJ - 6 V^3 drho,  d theta_XX = -V^2 dJ,
+    and the reconstruction adds (1 - 1/s) d theta to the post-collision
+    moments, which removes (1 - 1/s_e) d theta_E / 6 + (1 - 1/s_xx) d theta_XX / 2
+    from the viscous flux.  For the 2x2 system with flux Jacobian
+    [[0, 1], [1/3 - V^2, 2 V]] the wave of speed V +- c (c = 1/sqrt 3) is
+    damped at D/2 +- (D V - E') / (2 c), per step and per k^2."""
+    if s_xx is None:
+        s_xx = s_of_nu(nu)
+    zeta = (1 / s_e - 0.5) / 3
+    D = (nu + zeta) * (1 - 4.5 * V * V)
+    E = (nu + zeta) * V * (1 - 3 * V * V)
+    if printed_theta:
+        D -= (1 - 1 / s_e) * 15 * V * V / 6 - (1 - 1 / s_xx) * V * V / 2
+        E -= (1 - 1 / s_e) * V ** 3
+    c = 1 / np.sqrt(3)
+    return D / 2 - (D * V - E) / (2 * c), D / 2 + (D * V - E) / (2 * c)
+
+
+@pytest.mark.parametrize("stencil", [3, 5])
+def test_sound_damping_in_mean_flow_closed_form(oracle, stencil):
+    """Sec. 2: damping of both sound waves carried by a mean flow V, at every
+    order in V, equals the hand-derived rates of the printed theta
+    (sound_rates_in_mean_flow).  This fixes the v^2 and v.grad(rho) terms of
+    theta_E and theta_XX, which no test at rest can see.  The paper states
+    that with its expressions the viscosities are those of D2Q9; the printed
+    theta gives D2Q9's shear damping (test above) but shifts the sound
+    damping by -V^2 (5/4 (1 - 1/s_e) - 1/4 (1 - 1/s_xx)) per k^2, so that
+    sound grows at V = 0.2 for s_e = 1.8."""
+    nu = 0.01
+    for s_e in (1.2, 1.5, 1.8):
+        p = oracle.params(256, 1, stencil, s_of_nu(nu), s_e)
+        e0 = sound_rates_in_mean_flow(nu, s_e, 0.0)[0]
+        (_, g0m), _, (_, g0p) = _sound_modes(oracle, p, 0.0)
+        for V in (0.05, 0.1, 0.2):
+            (cm, gm), _, (cp, gp) = _sound_modes(oracle, p, V)
+            em, ep = sound_rates_in_mean_flow(nu, s_e, V)
+            # the shift caused by V; the rates at rest carry the stencil's
+            # k^4 hyperviscosity (pinned by Table 1), which the shift cancels
+            assert abs((gm - g0m) - (em - e0)) < 1.5e-3 * e0, (s_e, V, gm, em)
+            assert abs((gp - g0p) - (ep - e0)) < 1.5e-3 * e0, (s_e, V, gp, ep)
+    # the sign change the closed form predicts
+    p = oracle.params(128, 1, stencil, s_of_nu(nu), 1.8)
+    (_, gm), _, (_, gp) = _sound_modes(oracle, p, 0.2)
+    assert gm < 0 and gp < 0
+
+
+def test_mrt_sound_damping_in_mean_flow_closed_form(oracle):
+    """Sec. 1-a: the MRT step's sound waves in a mean flow V are damped at
+    the D2Q9 rates (nu + zeta)(1 - 9/2 V^2)/2 -+ 3/4 (nu + zeta) V^3 / c,
+    independent of s_e apart from zeta (sound_rates_in_mean_flow with the
+    full theta)."""
+    nu = 0.01
+    for s_e in (1.2, 1.5, 1.8):
+        p = oracle.params(128, 1, oracle.MRT, s_of_nu(nu), s_e, 1.2, 1.5)
+        g0 = sound_rates_in_mean_flow(nu, s_e, 0.0, printed_theta=False)[0]
+        for V in (0.05, 0.1, 0.2):
+            modes = _mrt_modes(oracle, p, V)
+            (cm, gm), (cp, gp) = modes[0], modes[-1]
+            assert abs(cm - (V - 1 / np.sqrt(3))) < 1e-3 and abs(cp - (V + 1 / np.sqrt(3))) < 1e-3
+            em, ep = sound_rates_in_mean_flow(nu, s_e, V, printed_theta=False)
+            assert abs(gm - em) < 1e-3 * g0 and abs(gp - ep) < 1e-3 * g0, (s_e, V, gm, em, gp, ep)
+
+
 def _poiseuille(oracle, scheme, N, xi, nu, umax, s_q=None, nx=4):
     s_xx = s_of_nu(nu)
     H = N - 1 + 2 * xi

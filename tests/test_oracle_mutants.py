@@ -1,7 +1,7 @@
 """The oracle's pins would catch a plausible mistake: each test plants one
 mistake in a copy of the oracle's source (on the CPU), builds it, and checks
 that at least one pin (Table 1 via the Jacobian, the closed-form shear
-wave, conservation, the Poiseuille curvature, the mean-flow viscosity)
+wave, the Poiseuille curvature, the damping of sound in a mean flow)
 rejects the mutant while the unmodified oracle passes them all."""
 import ctypes
 import os
@@ -29,6 +29,13 @@ MUTANTS = {
                          "                    const int si = wrap(i + CX[a], nx);\n                    int sj = j + CY[a];\n                    if (!walls) sj = wrap(sj, ny);\n                    f[a] = fstar"),
     # second half of the force dropped
     "half_force": ("m[1] = Jx + 0.5 * p->force_x;", "m[1] = Jx;"),
+    # terms of theta that vanish at rest and only a mean flow sees
+    "theta_e_v2": ("(2.0 + 6.0 * (vx * vx + vy * vy)) * (dx_Jx + dy_Jy)",
+                   "(2.0 + 0.0 * (vx * vx + vy * vy)) * (dx_Jx + dy_Jy)"),
+    "theta_e_rho": ("2.0 * (vx * drx + vy * dry);", "4.0 * (vx * drx + vy * dry);"),
+    "theta_xx_rho": ("(2.0 / 3.0) * (vx * drx - vy * dry)", "(1.0 / 3.0) * (vx * drx - vy * dry)"),
+    "theta_xx_flux": ("2.0 * (vx * (dx_Pxx + dy_Pxy) - vy * (dx_Pxy + dy_Pyy))",
+                      "1.0 * (vx * (dx_Pxx + dy_Pxy) - vy * (dx_Pxy + dy_Pyy))"),
 }
 
 # LW-ACM (Sec. 1-b), checked by its own pins
@@ -104,6 +111,16 @@ def _pins_pass(ref):
     curv = -np.polyfit(yy[4:12], u[4:12], 2)[0]
     if abs(curv / (F / (2 * nu)) - 1) > 2e-5:
         failures.append("poiseuille")
+    # 4. sound damping in a mean flow against its hand-derived rates, five points
+    import test_oracle_closed_forms as C
+    nu, s_e, V = 0.01, 1.5, 0.1
+    ps = ref.params(256, 1, 5, 1 / (3 * nu + 0.5), s_e)
+    e0 = C.sound_rates_in_mean_flow(nu, s_e, 0.0)[0]
+    (_, g0m), _, (_, g0p) = C._sound_modes(ref, ps, 0.0)
+    (_, gm), _, (_, gp) = C._sound_modes(ref, ps, V)
+    em, ep = C.sound_rates_in_mean_flow(nu, s_e, V)
+    if max(abs((gm - g0m) - (em - e0)), abs((gp - g0p) - (ep - e0))) > 1.5e-3 * e0:
+        failures.append("mean_flow_sound")
     return failures
 
 
