@@ -66,3 +66,23 @@ def test_built_for_sm103a():
     """The build passes -gencode arch=compute_103a,code=sm_103a to nvcc."""
     from paper_1803_00437_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_missing_library_raises(tmp_path):
+    """The binding has no CPU fallback: without the built library it raises."""
+    from paper_1803_00437_gb300 import fdlbm
+    with pytest.raises(fdlbm.FdlbmError):
+        fdlbm.load_library(str(tmp_path / "libfdlbm.so"))
+
+
+def test_no_gpu_no_lattice():
+    """Without a GPU, creating a lattice or a batch fails instead of running
+    anywhere else."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1803_00437_gb300 import fdlbm as F
+    with pytest.raises((RuntimeError, AssertionError, F.FdlbmError)):
+        F.Lattice(F.LatticeConfig(64, 64, "fd5"))
+    with pytest.raises((RuntimeError, AssertionError, F.FdlbmError)):
+        F.Batch("fd5", max_lattices=4, max_side=64, arena_bytes=1 << 20)
