@@ -62,6 +62,13 @@ extern "C" {
 #define FDLBM_SCHEME_FD3 3   /* FD-LBM, three-point differences (Sec. 2)   */
 #define FDLBM_SCHEME_FD5 5   /* FD-LBM, five-point differences (Sec. 2)    */
 #define FDLBM_SCHEME_MRT 100 /* multiple-relaxation-time D2Q9 (Sec. 1-a)  */
+/* FD-LBM with the nine-point differences of Sec. 2 (D2Q9 footprint):
+ * d_x f = f(i+1,j) - f(i-1,j) - [f(i+1,j+1) - f(i-1,j+1) + f(i+1,j-1)
+ * - f(i-1,j-1)] / 4, d_y alike.  Same state, storage, walls and force as the
+ * other FD-LBM stencils; always the tiled kernel (FDLBM_FLAG_STREAM is
+ * FDLBM_ERR_UNSUPPORTED).  Linearly unstable at short wavelengths for small
+ * viscosities (Sec. 3-a; max |z| about 1.2 at nu = 0.01, 1 near nu = 0.15). */
+#define FDLBM_SCHEME_FD9 9
 /* Link-wise artificial compressibility method (Sec. 1-b, Eq. 3): every link
  * rebuilt from equilibria alone, f_a(x) = feq_a(x - c_a) + Theta (feo_a(x) -
  * feo_a(x - c_a)), feo the odd part of feq, Theta = 1 - 6 nu, nu from s_xx as

@@ -2,7 +2,8 @@
 // staged in shared memory with a halo of r + 1 nodes.  Handles periodic and
 // channel (walls in y) lattices of any size and FP32 / FP16 / BF16 storage.
 // Stencil radius r = 0 is LW-ACM (Sec. 1-b, Eq. 3): no finite differences,
-// a one-node halo for the gather.
+// a one-node halo for the gather.  The nine-point stencil of Sec. 2 has
+// radius 1 and also reads the diagonal neighbours, which the 2-D tile holds.
 //
 // Per CTA (TX x TY outputs):
 //   1. load (rho-1, u) of the tile plus a halo of H = r + 1 nodes (gradients
@@ -45,7 +46,14 @@ __device__ __forceinline__ void lw_reconstruct(float dr, float Jx, float Jy, flo
     g[8] = dm - smm;
 }
 
-template <int R, bool WALLS, typename T>
+// Nine-point difference (Sec. 2, D2Q9 footprint) along the axis of stride s,
+// the other axis having stride t:
+//   d = f(+s) - f(-s) - [(f(+s+t) - f(-s+t)) + (f(+s-t) - f(-s-t))] / 4
+__device__ __forceinline__ float fd_deriv9(const float* p, int s, int t) {
+    return (p[s] - p[-s]) - 0.25f * ((p[s + t] - p[-s + t]) + (p[s - t] - p[-s - t]));
+}
+
+template <int R, bool NINE, bool WALLS, typename T>
 __global__ void __launch_bounds__(kThreads)
     fd_step_tiled_kernel(FdState<T> src, FdState<T> dst, int nx, int ny, size_t pitch,
                          FdCoeffs c, float lw_t) {
@@ -87,16 +95,29 @@ __global__ void __launch_bounds__(kThreads)
             continue;
         }
         NodeDerivs d;
-        d.drx = fd_deriv<R>(&sf[0][l], 1);
-        d.dry = fd_deriv<R>(&sf[0][l], LX);
-        d.dJx_x = fd_deriv<R>(&sf[3][l], 1);
-        d.dJx_y = fd_deriv<R>(&sf[3][l], LX);
-        d.dJy_x = fd_deriv<R>(&sf[4][l], 1);
-        d.dJy_y = fd_deriv<R>(&sf[4][l], LX);
-        d.dPxx_x = fd_deriv<R>(&sf[5][l], 1);
-        d.dPxy_x = fd_deriv<R>(&sf[6][l], 1);
-        d.dPxy_y = fd_deriv<R>(&sf[6][l], LX);
-        d.dPyy_y = fd_deriv<R>(&sf[7][l], LX);
+        if (NINE) {
+            d.drx = fd_deriv9(&sf[0][l], 1, LX);
+            d.dry = fd_deriv9(&sf[0][l], LX, 1);
+            d.dJx_x = fd_deriv9(&sf[3][l], 1, LX);
+            d.dJx_y = fd_deriv9(&sf[3][l], LX, 1);
+            d.dJy_x = fd_deriv9(&sf[4][l], 1, LX);
+            d.dJy_y = fd_deriv9(&sf[4][l], LX, 1);
+            d.dPxx_x = fd_deriv9(&sf[5][l], 1, LX);
+            d.dPxy_x = fd_deriv9(&sf[6][l], 1, LX);
+            d.dPxy_y = fd_deriv9(&sf[6][l], LX, 1);
+            d.dPyy_y = fd_deriv9(&sf[7][l], LX, 1);
+        } else {
+            d.drx = fd_deriv<R>(&sf[0][l], 1);
+            d.dry = fd_deriv<R>(&sf[0][l], LX);
+            d.dJx_x = fd_deriv<R>(&sf[3][l], 1);
+            d.dJx_y = fd_deriv<R>(&sf[3][l], LX);
+            d.dJy_x = fd_deriv<R>(&sf[4][l], 1);
+            d.dJy_y = fd_deriv<R>(&sf[4][l], LX);
+            d.dPxx_x = fd_deriv<R>(&sf[5][l], 1);
+            d.dPxy_x = fd_deriv<R>(&sf[6][l], 1);
+            d.dPxy_y = fd_deriv<R>(&sf[6][l], LX);
+            d.dPyy_y = fd_deriv<R>(&sf[7][l], LX);
+        }
         fd_reconstruct(sf[0][l], sf[1][l], sf[2][l], d, c, g);
 #pragma unroll
         for (int a = 0; a < 9; ++a) sg[a][t] = g[a];
@@ -143,7 +164,7 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <int R, bool WALLS, typename T>
+template <int R, bool NINE, bool WALLS, typename T>
 cudaError_t launch_typed(fdlbm_s* h, const void* src, void* dst) {
     const size_t plane = h->L.plane;
     const T* s = static_cast<const T*>(src);
@@ -158,22 +179,24 @@ cudaError_t launch_typed(fdlbm_s* h, const void* src, void* dst) {
     c.xi = (float)h->p.wall_xi;
     const float lw_t = (float)(2.0 * (1.0 / h->p.s_xx - 0.5) / 3.0);  // LW-ACM: 2 nu
     dim3 grid((h->p.nx + kTX - 1) / kTX, (h->p.ny + kTY - 1) / kTY);
-    fd_step_tiled_kernel<R, WALLS, T>
+    fd_step_tiled_kernel<R, NINE, WALLS, T>
         <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c, lw_t);
     return cudaGetLastError();
 }
 
-template <int R, typename T>
+template <int R, bool NINE, typename T>
 cudaError_t launch_boundary(fdlbm_s* h, const void* src, void* dst) {
-    if (h->p.boundary == FDLBM_BOUNDARY_WALLS_Y) return launch_typed<R, true, T>(h, src, dst);
-    return launch_typed<R, false, T>(h, src, dst);
+    if (h->p.boundary == FDLBM_BOUNDARY_WALLS_Y)
+        return launch_typed<R, NINE, true, T>(h, src, dst);
+    return launch_typed<R, NINE, false, T>(h, src, dst);
 }
 
 template <typename T>
 cudaError_t launch_stencil(fdlbm_s* h, const void* src, void* dst) {
-    if (h->p.scheme == FDLBM_SCHEME_LWACM) return launch_typed<0, false, T>(h, src, dst);
-    if (h->p.scheme == FDLBM_SCHEME_FD3) return launch_boundary<1, T>(h, src, dst);
-    return launch_boundary<2, T>(h, src, dst);
+    if (h->p.scheme == FDLBM_SCHEME_LWACM) return launch_typed<0, false, false, T>(h, src, dst);
+    if (h->p.scheme == FDLBM_SCHEME_FD3) return launch_boundary<1, false, T>(h, src, dst);
+    if (h->p.scheme == FDLBM_SCHEME_FD9) return launch_boundary<1, true, T>(h, src, dst);
+    return launch_boundary<2, false, T>(h, src, dst);
 }
 
 }  // namespace

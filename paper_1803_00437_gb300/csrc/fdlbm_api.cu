@@ -48,8 +48,9 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->nx < 1 || p->ny < 1 || p->nx > 65535 || p->ny > 65535)
         return fail(FDLBM_ERR_INVALID, "nx and ny must lie in [1, 65535]");
     if (p->scheme != FDLBM_SCHEME_FD3 && p->scheme != FDLBM_SCHEME_FD5 &&
-        p->scheme != FDLBM_SCHEME_MRT && p->scheme != FDLBM_SCHEME_LWACM)
-        return fail(FDLBM_ERR_INVALID, "scheme must be FD3, FD5, MRT or LWACM");
+        p->scheme != FDLBM_SCHEME_FD9 && p->scheme != FDLBM_SCHEME_MRT &&
+        p->scheme != FDLBM_SCHEME_LWACM)
+        return fail(FDLBM_ERR_INVALID, "scheme must be FD3, FD5, FD9, MRT or LWACM");
     if (p->boundary != FDLBM_BOUNDARY_PERIODIC && p->boundary != FDLBM_BOUNDARY_WALLS_Y)
         return fail(FDLBM_ERR_INVALID, "boundary must be PERIODIC or WALLS_Y");
     if (p->storage != FDLBM_STORAGE_F32 && p->storage != FDLBM_STORAGE_F16 &&
@@ -77,6 +78,8 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->scheme == FDLBM_SCHEME_LWACM &&
         (p->boundary != FDLBM_BOUNDARY_PERIODIC || p->force_x != 0.0 || p->force_y != 0.0))
         return fail(FDLBM_ERR_UNSUPPORTED, "LWACM: periodic lattices without force only");
+    if (p->scheme == FDLBM_SCHEME_FD9 && (p->flags & FDLBM_FLAG_STREAM))
+        return fail(FDLBM_ERR_UNSUPPORTED, "FD9 runs on the tiled kernel only");
     return FDLBM_OK;
 }
 
@@ -444,7 +447,8 @@ cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
     // the streaming kernel pays off once the lattice fills the GPU's warps
     constexpr int64_t kStreamMinNodes = 1 << 20;
     const bool big = (int64_t)h->p.nx * h->p.ny >= kStreamMinNodes;
-    if (h->fd_path != 1 && fd_stream_supported(h->p) && (big || h->fd_path == 2))
+    if (h->p.scheme != FDLBM_SCHEME_FD9 && h->fd_path != 1 && fd_stream_supported(h->p) &&
+        (big || h->fd_path == 2))
         return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }

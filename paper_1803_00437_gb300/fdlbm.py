@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libfdlbm.so")
 # include/fdlbm.h constants
 OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT = (
     0, -1, -2, -3, -4, -5, -6)
-SCHEMES = {"fd3": 3, "fd5": 5, "mrt": 100, "lwacm": 200}
+SCHEMES = {"fd3": 3, "fd5": 5, "fd9": 9, "mrt": 100, "lwacm": 200}
 BOUNDARIES = {"periodic": 0, "walls_y": 1}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}

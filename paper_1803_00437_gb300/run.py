@@ -17,7 +17,7 @@ import json
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--side", type=int, default=4096)
-    ap.add_argument("--scheme", default="fd5", choices=["fd3", "fd5", "mrt", "lwacm"])
+    ap.add_argument("--scheme", default="fd5", choices=["fd3", "fd5", "fd9", "mrt", "lwacm"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--nu", type=float, default=0.01)

@@ -4,7 +4,7 @@ import numpy as np
 
 from paper_1803_00437_gb300 import inputs
 
-SCHEME_TO_ORACLE = {"fd3": 3, "fd5": 5, "mrt": 100, "lwacm": 200}
+SCHEME_TO_ORACLE = {"fd3": 3, "fd5": 5, "fd9": 9, "mrt": 100, "lwacm": 200}
 BOUNDARY_TO_ORACLE = {"periodic": 0, "walls_y": 1}
 
 

@@ -40,7 +40,8 @@ def test_workspace_size_validates(lib):
            F.LatticeConfig(4, 4, "mrt", storage="f16"),
            F.LatticeConfig(4, 1, boundary="walls_y"),
            F.LatticeConfig(4, 4, "mrt", boundary="walls_y", wall_xi=0.3),
-           F.LatticeConfig(4, 4, boundary="walls_y", wall_xi=0.0)]
+           F.LatticeConfig(4, 4, boundary="walls_y", wall_xi=0.0),
+           F.LatticeConfig(256, 64, "fd9", flags=F.FLAG_STREAM)]
     for cfg in bad:
         assert F.workspace_size(cfg) == 0, cfg
     f32 = F.workspace_size(F.LatticeConfig(512, 48, "fd5"))
@@ -48,6 +49,10 @@ def test_workspace_size_validates(lib):
     assert f32 - f16 == 2 * 3 * 512 * 48 * 2
     mrt = F.workspace_size(F.LatticeConfig(64, 48, "mrt"))
     assert mrt > n
+    # nine points: same state as the other FD-LBM stencils, walls and force allowed
+    assert F.workspace_size(F.LatticeConfig(64, 48, "fd9")) == n
+    assert F.workspace_size(F.LatticeConfig(64, 48, "fd9", boundary="walls_y", wall_xi=0.5,
+                                            force=(1e-5, 0.0))) == n
 
 
 def test_status_strings_and_null_handles(lib):
