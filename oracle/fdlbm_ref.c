@@ -37,6 +37,12 @@
  *     extrapolated to zero at the wall, from the first fluid row when
  *     xi >= 1/2 and from the second when xi < 1/2; rho is copied from the
  *     first fluid row.  MRT uses half-way bounce-back (wall at xi = 1/2).
+ *   - Curved walls (Sec. 3-b): the same closure along a lattice link.  Each
+ *     virtual node comes with the link along which its straight line reaches
+ *     the fluid and the wall's distance xi before the first fluid node on it;
+ *     u is extrapolated to zero at the wall from the first fluid node
+ *     (xi >= 1/2) or the second (xi < 1/2), rho copied from the first.  For a
+ *     straight channel this is the closure above.
  */
 #include "fdlbm_ref.h"
 
@@ -130,13 +136,79 @@ typedef struct {
     const double* rho;
     const double* ux;
     const double* uy;
+    /* curved walls (Sec. 3-b); kind == NULL without them */
+    const uint8_t* kind;
+    const int32_t* vslot;  /* per node: index into the virtual-node table, or -1 */
+    const int8_t* vlink;
+    const double* vxi;
+    int* bad;              /* set when an unused node would be read */
 } fields_t;
+
+static void mark_bad(const fields_t* F) {
+#pragma omp atomic write
+    *F->bad = 1;
+}
+
+static int kind_at(const fields_t* F, int i, int j) {
+    const int nx = F->p->nx, ny = F->p->ny;
+    return F->kind[(int64_t)wrap(j, ny) * nx + wrap(i, nx)];
+}
+
+/* State of a node of a lattice with curved walls (Sec. 3-b).  Fluid nodes
+ * hold their own state.  A virtual node lies outside the fluid, on a
+ * straight line along link a that reaches the first fluid node after d
+ * links; the wall crosses the line at t_w = d - xi (t counted in links from
+ * the virtual node).  Its velocity is the linear extrapolation, through
+ * u = 0 at t_w, of the velocity at t_ref = d (first fluid node, xi >= 1/2)
+ * or t_ref = d + 1 (second, xi < 1/2): u(0) = u(t_ref) (0 - t_w) /
+ * (t_ref - t_w).  Its density is that of the first fluid node. */
+static void walled_node_state(const fields_t* F, int i, int j, double* r, double* vx,
+                              double* vy) {
+    const int nx = F->p->nx, ny = F->p->ny;
+    i = wrap(i, nx);
+    j = wrap(j, ny);
+    const int64_t idx = (int64_t)j * nx + i;
+    *r = 1.0;
+    *vx = 0.0;
+    *vy = 0.0;
+    if (F->kind[idx] == 0) {
+        *r = F->rho[idx];
+        *vx = F->ux[idx];
+        *vy = F->uy[idx];
+        return;
+    }
+    if (F->kind[idx] != 1) {
+        mark_bad(F);
+        return;
+    }
+    const int t = F->vslot[idx];
+    const int a = F->vlink[t];
+    const double xi = F->vxi[t];
+    int d = 1;
+    while (d <= 16 && kind_at(F, i + d * CX[a], j + d * CY[a]) != 0) ++d;
+    const int tref = (xi >= 0.5) ? d : d + 1;
+    if (d > 16 || kind_at(F, i + tref * CX[a], j + tref * CY[a]) != 0) {
+        mark_bad(F);
+        return;
+    }
+    const double tw = (double)d - xi;
+    const double factor = (0.0 - tw) / ((double)tref - tw);
+    const int64_t first = (int64_t)wrap(j + d * CY[a], ny) * nx + wrap(i + d * CX[a], nx);
+    const int64_t ref = (int64_t)wrap(j + tref * CY[a], ny) * nx + wrap(i + tref * CX[a], nx);
+    *r = F->rho[first];
+    *vx = F->ux[ref] * factor;
+    *vy = F->uy[ref] * factor;
+}
 
 /* Primitive state at (i, j).  Rows outside 0..ny-1 are periodic images, or,
  * with walls, virtual fluid nodes whose velocity is the linear extrapolation
  * to zero at the wall (Sec. 3-b) and whose density is that of the first
  * fluid row. */
 static void node_state(const fields_t* F, int i, int j, double* r, double* vx, double* vy) {
+    if (F->kind) {
+        walled_node_state(F, i, j, r, vx, vy);
+        return;
+    }
     const int nx = F->p->nx, ny = F->p->ny;
     i = wrap(i, nx);
     if (F->p->boundary == FDLBM_REF_PERIODIC) j = wrap(j, ny);
@@ -260,7 +332,7 @@ int fdlbm_ref_fd_fstar(const fdlbm_ref_params* p, const double* rho, const doubl
         return FDLBM_REF_EINVAL;
     double Minv[9][9];
     inverse_moment_matrix(Minv);
-    fields_t F = {p, rho, ux, uy};
+    fields_t F = {p, rho, ux, uy, NULL, NULL, NULL, NULL, NULL};
     fd_reconstruct(&F, Minv, i, j, fstar9);
     return FDLBM_REF_OK;
 }
@@ -298,7 +370,7 @@ int fdlbm_ref_fd_step(const fdlbm_ref_params* p, double* rho, double* ux, double
     (void)nthr;
 
     for (int64_t n = 0; n < nsteps; ++n) {
-        fields_t F = {p, rho, ux, uy};
+        fields_t F = {p, rho, ux, uy, NULL, NULL, NULL, NULL, NULL};
 #pragma omp parallel for schedule(static) num_threads(nthr)
         for (int j = jlo; j <= jhi; ++j) {
             for (int i = 0; i < nx; ++i) {
@@ -329,6 +401,88 @@ int fdlbm_ref_fd_step(const fdlbm_ref_params* p, double* rho, double* ux, double
     return FDLBM_REF_OK;
 }
 
+int fdlbm_ref_fd_step_walls(const fdlbm_ref_params* p, const uint8_t* kind, int64_t nvirt,
+                            const int64_t* vnode, const int8_t* vlink, const double* vxi,
+                            double* rho, double* ux, double* uy, int64_t nsteps) {
+    if (!valid_params(p) || p->scheme == FDLBM_REF_MRT || p->scheme == FDLBM_REF_LWACM ||
+        p->boundary != FDLBM_REF_PERIODIC || !kind || !rho || !ux || !uy || nsteps < 0 ||
+        nvirt < 0 || (nvirt > 0 && (!vnode || !vlink || !vxi)))
+        return FDLBM_REF_EINVAL;
+    const int nx = p->nx, ny = p->ny;
+    const int64_t nodes = (int64_t)nx * ny;
+    int32_t* vslot = (int32_t*)malloc(sizeof(int32_t) * (size_t)nodes);
+    double* fstar = (double*)malloc(sizeof(double) * 9 * (size_t)nodes);
+    uint8_t* source = (uint8_t*)calloc((size_t)nodes, 1); /* fluid nodes and their neighbours */
+    if (!vslot || !fstar || !source) {
+        free(vslot);
+        free(fstar);
+        free(source);
+        return FDLBM_REF_ENOMEM;
+    }
+    int bad = 0;
+    for (int64_t n = 0; n < nodes; ++n) {
+        vslot[n] = -1;
+        if (kind[n] > 2) bad = 1;
+    }
+    for (int64_t t = 0; t < nvirt && !bad; ++t) {
+        if (vnode[t] < 0 || vnode[t] >= nodes || kind[vnode[t]] != 1 || vslot[vnode[t]] >= 0 ||
+            vlink[t] < 1 || vlink[t] > 8 || !(vxi[t] > 0.0 && vxi[t] <= 1.0))
+            bad = 1;
+        else
+            vslot[vnode[t]] = (int32_t)t;
+    }
+    for (int64_t n = 0; n < nodes && !bad; ++n)
+        if (kind[n] == 1 && vslot[n] < 0) bad = 1;
+    /* the nodes whose populations propagate into a fluid node (Eq. 2) */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            if (kind[(int64_t)j * nx + i] == 0)
+                for (int a = 0; a < 9; ++a)
+                    source[(int64_t)wrap(j - CY[a], ny) * nx + wrap(i - CX[a], nx)] = 1;
+    double Minv[9][9];
+    inverse_moment_matrix(Minv);
+    const int nthr = fdlbm_ref_get_threads();
+    (void)nthr;
+    for (int64_t step = 0; step < nsteps && !bad; ++step) {
+        fields_t F = {p, rho, ux, uy, kind, vslot, vlink, vxi, &bad};
+        /* reconstruction (Sec. 2) at the fluid nodes and the virtual nodes
+         * next to them */
+#pragma omp parallel for schedule(static) num_threads(nthr)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                const int64_t n = (int64_t)j * nx + i;
+                double fs[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                if (source[n]) fd_reconstruct(&F, Minv, i, j, fs);
+                for (int a = 0; a < 9; ++a) fstar[a * nodes + n] = fs[a];
+            }
+        }
+        /* propagation (Eq. 2) into the fluid nodes; their sources must not
+         * be unused nodes */
+#pragma omp parallel for schedule(static) num_threads(nthr)
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                const int64_t n = (int64_t)j * nx + i;
+                if (kind[n] != 0) continue;
+                double f[9];
+                for (int a = 0; a < 9; ++a) {
+                    const int64_t src = (int64_t)wrap(j - CY[a], ny) * nx + wrap(i - CX[a], nx);
+                    if (kind[src] == 2) mark_bad(&F);
+                    f[a] = fstar[a * nodes + src];
+                }
+                double r, vx, vy;
+                close_moments(p, f, &r, &vx, &vy);
+                rho[n] = r;
+                ux[n] = vx;
+                uy[n] = vy;
+            }
+        }
+    }
+    free(vslot);
+    free(fstar);
+    free(source);
+    return bad ? FDLBM_REF_EINVAL : FDLBM_REF_OK;
+}
+
 int fdlbm_ref_fd_step_points(const fdlbm_ref_params* p, const double* rho, const double* ux,
                              const double* uy, int64_t npts, const int64_t* idx, double* out) {
     if (!valid_params(p) || p->scheme == FDLBM_REF_MRT || !rho || !ux || !uy || npts < 0 ||
@@ -340,7 +494,7 @@ int fdlbm_ref_fd_step_points(const fdlbm_ref_params* p, const double* rho, const
         if (idx[t] < 0 || idx[t] >= (int64_t)nx * ny) return FDLBM_REF_EINVAL;
     double Minv[9][9];
     inverse_moment_matrix(Minv);
-    fields_t F = {p, rho, ux, uy};
+    fields_t F = {p, rho, ux, uy, NULL, NULL, NULL, NULL, NULL};
     const int nthr = fdlbm_ref_get_threads();
     (void)nthr;
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthr)

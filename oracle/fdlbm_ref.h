@@ -79,6 +79,21 @@ int fdlbm_ref_fd_step_points(const fdlbm_ref_params* p, const double* rho, const
 int fdlbm_ref_fd_fstar(const fdlbm_ref_params* p, const double* rho, const double* ux,
                        const double* uy, int32_t i, int32_t j, double* fstar9);
 
+/* FD-LBM with curved walls (Sec. 3-b) on a periodic lattice (boundary
+ * PERIODIC).  kind[j*nx+i]: 0 fluid, 1 virtual, 2 unused.  The nvirt
+ * virtual nodes are vnode[t] (flat index, kind 1, each listed once); the
+ * straight line from vnode[t] along link vlink[t] (1..8, Sec. 1 order)
+ * reaches the fluid, and the wall crosses it vxi[t] link lengths (0 < xi
+ * <= 1) before the first fluid node on it.  A virtual node, whenever read,
+ * takes rho of that first fluid node and u linearly extrapolated to zero at
+ * the wall from the first fluid node (xi >= 1/2) or the second (xi < 1/2).
+ * Only fluid nodes are advanced; the other entries of rho, ux, uy are left
+ * as they are.  FDLBM_REF_EINVAL if the scheme would read an unused node,
+ * if a line finds no fluid within 16 links or if the table is inconsistent. */
+int fdlbm_ref_fd_step_walls(const fdlbm_ref_params* p, const uint8_t* kind, int64_t nvirt,
+                            const int64_t* vnode, const int8_t* vlink, const double* vxi,
+                            double* rho, double* ux, double* uy, int64_t nsteps);
+
 /* MRT: populations at equilibrium for (rho, u) with J = rho*u - F/2, so that
  * the reported velocity at t = 0 equals u. */
 int fdlbm_ref_mrt_init(const fdlbm_ref_params* p, const double* rho, const double* ux,

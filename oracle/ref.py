@@ -75,10 +75,13 @@ def lib():
                                                              i64p, dp]
             L.fdlbm_ref_lwacm_step.argtypes = [pp, dp, dp, dp, ctypes.c_int64]
             L.fdlbm_ref_lwacm_step_points.argtypes = [pp, dp, dp, dp, ctypes.c_int64, i64p, dp]
+            u8p, i8p = ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ctypes.c_int8)
+            L.fdlbm_ref_fd_step_walls.argtypes = [pp, u8p, ctypes.c_int64, i64p, i8p, dp,
+                                                  dp, dp, dp, ctypes.c_int64]
             for name in ("fdlbm_ref_fd_step", "fdlbm_ref_fd_step_points", "fdlbm_ref_fd_fstar",
                          "fdlbm_ref_mrt_init", "fdlbm_ref_mrt_step", "fdlbm_ref_mrt_moments",
                          "fdlbm_ref_mrt_step_points_from_eq", "fdlbm_ref_lwacm_step",
-                         "fdlbm_ref_lwacm_step_points"):
+                         "fdlbm_ref_lwacm_step_points", "fdlbm_ref_fd_step_walls"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -127,6 +130,25 @@ def fd_run(p: Params, rho, ux, uy, nsteps: int):
     r, x, y = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
     _check(lib().fdlbm_ref_fd_step(ctypes.byref(p), _dptr(r), _dptr(x), _dptr(y), int(nsteps)),
            "fd_step")
+    return r, x, y
+
+
+def fd_run_walls(p: Params, walls, rho, ux, uy, nsteps: int):
+    """FD-LBM with curved walls (Sec. 3-b): `walls` carries kind [ny][nx]
+    (0 fluid, 1 virtual, 2 unused) and the virtual-node table (node, link,
+    xi).  Returns (rho, ux, uy) after nsteps; only fluid nodes change."""
+    shape = (p.ny, p.nx)
+    r, x, y = _f64(rho, shape), _f64(ux, shape), _f64(uy, shape)
+    kind = np.ascontiguousarray(walls.kind, dtype=np.uint8)
+    node = np.ascontiguousarray(walls.node, dtype=np.int64)
+    link = np.ascontiguousarray(walls.link, dtype=np.int8)
+    xi = np.ascontiguousarray(walls.xi, dtype=np.float64)
+    assert kind.shape == shape
+    _check(lib().fdlbm_ref_fd_step_walls(
+        ctypes.byref(p), kind.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), node.size,
+        node.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        link.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), _dptr(xi), _dptr(r), _dptr(x),
+        _dptr(y), int(nsteps)), "fd_step_walls")
     return r, x, y
 
 
