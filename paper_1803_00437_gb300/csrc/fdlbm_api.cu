@@ -316,11 +316,21 @@ int fdlbm_step(fdlbm_t* h, int64_t nsteps) {
     for (int64_t n = 0; n < nsteps; ++n) {
         void* src = state_ptr(h, h->cur);
         void* dst = state_ptr(h, 1 - h->cur);
+        if (h->walls) {  // curved walls: the virtual fluid the step reads (Sec. 3-b)
+            cudaError_t e = launch_walls_fill(h, src);
+            h->launches += 1;
+            if (e != cudaSuccess) return cuda_fail(h, e, "walls kernel");
+        }
         cudaError_t e = (h->p.scheme == FDLBM_SCHEME_MRT) ? launch_mrt_step(h, src, dst)
                                                            : launch_fd_step(h, src, dst);
         h->launches += 1;
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
         h->cur = 1 - h->cur;
+    }
+    if (h->walls) {
+        cudaError_t e = launch_walls_fill(h, state_ptr(h, h->cur));
+        h->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(h, e, "walls kernel");
     }
     return FDLBM_OK;
 }

@@ -103,6 +103,8 @@ struct fdlbm_s {
     int64_t launches;
     int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
     int fd_path;            // 0: automatic, 1: tiled FD kernel, 2: streaming where it qualifies
+    const void* walls;      // curved walls: device table of closure entries (NULL: none)
+    int64_t walls_n;        // its number of entries
     // page-locked host landing area for reduction results and the device
     // status word (one synchronisation per reduction); NULL if unavailable
     struct HostIO {
@@ -131,6 +133,7 @@ constexpr int kMaxModes = 64;
 cudaError_t launch_modes_eval(fdlbm_s* h, int n_modes, const double* modes_host, double mean_ux,
                               double mean_uy, float* drho, float* ux, float* uy);
 cudaError_t launch_moments(fdlbm_s* h, const void* state, float* drho, float* ux, float* uy);
+cudaError_t launch_walls_fill(fdlbm_s* h, void* state);
 cudaError_t launch_reduce(fdlbm_s* h, const void* state, int what, double a0, double a1,
                           double* partial, double* result);
 

@@ -122,6 +122,10 @@ def load_library(path: str | None = None):
                      "fdlbm_batch_moments", "fdlbm_batch_reduce", "fdlbm_batch_sync",
                      "fdlbm_batch_set_segment_rows", "fdlbm_batch_set_grid"):
             getattr(L, name).restype = ctypes.c_int
+        L.fdlbm_walls_table_bytes.argtypes = [pp]
+        L.fdlbm_walls_table_bytes.restype = ctypes.c_size_t
+        L.fdlbm_set_walls.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_size_t]
+        L.fdlbm_set_walls.restype = ctypes.c_int
         L.fdlbm_reduce_fields_static.argtypes = [fp, fp, fp, ctypes.c_int32, ctypes.c_int32,
                                                  ctypes.c_int32, fp, fp, vp]
         L.fdlbm_reduce_fields_static.restype = ctypes.c_int
@@ -249,6 +253,32 @@ class Lattice:
         """drho, ux, uy: float32 CUDA tensors [ny, nx]."""
         self._check(self.lib.fdlbm_init(self._h, self._field(drho), self._field(ux),
                                         self._field(uy)), "init")
+
+    def set_walls(self, walls):
+        """Curved walls (Sec. 3-b, fdlbm_set_walls): `walls` carries kind
+        [ny, nx] (0 fluid, 1 virtual, 2 unused) and, per virtual node, node
+        (flat index), link (1..8) and xi; None removes them.  The device
+        table is a torch uint8 tensor kept with the lattice."""
+        import torch
+        if walls is None:
+            self._check(self.lib.fdlbm_set_walls(self._h, None, 0, None, None, None, None, 0),
+                        "set_walls")
+            self._walls_table = None
+            return
+        kind = np.ascontiguousarray(walls.kind, dtype=np.uint8)
+        node = np.ascontiguousarray(walls.node, dtype=np.int64)
+        link = np.ascontiguousarray(walls.link, dtype=np.int8)
+        xi = np.ascontiguousarray(walls.xi, dtype=np.float64)
+        if kind.shape != (self.cfg.ny, self.cfg.nx):
+            raise ValueError("kind must be [ny, nx]")
+        nbytes = int(self.lib.fdlbm_walls_table_bytes(ctypes.byref(self.params)))
+        table = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
+        self._check(self.lib.fdlbm_set_walls(
+            self._h, ctypes.c_void_p(kind.ctypes.data), node.size,
+            ctypes.c_void_p(node.ctypes.data), ctypes.c_void_p(link.ctypes.data),
+            ctypes.c_void_p(xi.ctypes.data), ctypes.c_void_p(table.data_ptr()), nbytes),
+            "set_walls")
+        self._walls_table = table
 
     def init_host(self, drho, ux, uy):
         """drho, ux, uy: host arrays [ny, nx] (converted to float32)."""

@@ -24,8 +24,8 @@ def lib():
 
 
 def test_every_declared_symbol_is_exported(lib):
-    names = _declared("fdlbm.h")
-    assert len(names) >= 15
+    names = _declared("fdlbm.h") + _declared("fdlbm_walls.h")
+    assert len(names) >= 17 and "fdlbm_set_walls" in names
     for n in names:
         assert hasattr(lib, n), n
 

@@ -78,3 +78,27 @@ def test_reading_an_unused_node_is_an_error(oracle):
     d, ux, uy = inputs.stokes_disk_mode(N, N, 15.0, 0, 3.8317, 1e-4)
     with pytest.raises(RuntimeError):
         oracle.fd_run_walls(oracle.params(N, N, 5, 1.7, 1.5), walls, 1 + d, ux, uy, 1)
+
+
+def printed_tables_2_3():
+    """Rows (table, kind, l, bessel, fd3, fd5) of Tables 2 and 3 as printed."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "tables2_3_stokes_disk.txt")
+    rows = []
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            t, kind, l, b, e3, e5 = ln.split()
+            rows.append((int(t), kind, int(l), float(b), float(e3), float(e5)))
+    return rows
+
+
+def test_bessel_column_is_the_mode_set():
+    """The Bessel column of Tables 2 and 3 is a^2 for the singlets l = 1..6
+    (a the l-th zero of J_1, stream function J_0) and for the doublets
+    m = 1..11 (a the first zero of J_{m+1}, stream function J_m cos(m theta)):
+    the modes that stokes_disk_mode builds.  Printed to 4-5 decimals."""
+    from scipy.special import jn_zeros
+    for t, kind, l, bessel, _, _ in printed_tables_2_3():
+        a = jn_zeros(1, l)[l - 1] if kind == "singlet" else jn_zeros(l + 1, 1)[0]
+        assert abs(a * a - bessel) <= 1e-4, (t, kind, l, a * a, bessel)
