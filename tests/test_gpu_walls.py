@@ -151,3 +151,50 @@ def test_tables_2_and_3_stokes_modes_in_a_disk(oracle, nu):
         g = _gpu_disk_rate("fd5", nu, m, a)
         o = W.disk_rate(oracle, 5, nu, m, a)
         assert abs(g / o - 1) <= 1e-4, (kind, l, g, o)
+
+
+def test_half_storage_with_walls(oracle):
+    """FP16 storage of (rho - 1, u), FP32 arithmetic: fluid nodes within
+    2e-3 of the amplitude of the FP64 oracle after 300 steps."""
+    from oracle import ref
+    walls, fluid, f = _disk_fields(68, 68, 29.9, seed=5)
+    lat = _lattice(68, 68, "fd5", walls, f, s_xx=_s(0.05), s_e=1.5, storage="f16")
+    lat.step(300)
+    gpu = _moments(lat)
+    r, x, y = ref.fd_run_walls(ref.params(68, 68, 5, _s(0.05), 1.5), walls,
+                               1 + f[0].astype(np.float64), f[1], f[2], 300)
+    amp = max(np.abs(f[1]).max(), np.abs(f[2]).max())
+    err = max(np.abs(g[fluid] - o[fluid]).max() for g, o in zip(gpu, (r - 1, x, y)))
+    assert err <= 2e-3 * amp
+
+
+def test_set_walls_rejects_inconsistent_tables():
+    """fdlbm_set_walls validates the geometry on the host and leaves the
+    lattice without walls when it refuses one."""
+    import dataclasses
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    N = 40
+    good = inputs.disk_walls(N, N, 15.0, reach=3)
+    lat = F.Lattice(F.LatticeConfig(N, N, "fd5"))
+    bad_cases = [
+        dataclasses.replace(good, kind=np.where(good.kind == 2, 3, good.kind).astype(np.uint8)),
+        dataclasses.replace(good, node=good.node[1:], link=good.link[1:], xi=good.xi[1:]),
+        dataclasses.replace(good, link=np.where(np.arange(good.link.size) == 0, 9,
+                                                good.link).astype(np.int8)),
+        dataclasses.replace(good, xi=np.where(np.arange(good.xi.size) == 0, 0.0, good.xi)),
+        inputs.disk_walls(N, N, 15.0, reach=2),  # five points read three nodes deep
+    ]
+    for w in bad_cases:
+        with pytest.raises(F.FdlbmError) as e:
+            lat.set_walls(w)
+        assert e.value.status == F.ERR_INVALID
+    lat.set_walls(good)
+    lat.set_walls(None)
+    for scheme in ("mrt", "lwacm"):
+        with pytest.raises(F.FdlbmError) as e:
+            F.Lattice(F.LatticeConfig(N, N, scheme)).set_walls(good)
+        assert e.value.status == F.ERR_UNSUPPORTED
+    with pytest.raises(F.FdlbmError):
+        F.Lattice(F.LatticeConfig(N, N, "fd5", boundary="walls_y", wall_xi=0.5)).set_walls(good)
+    torch.cuda.synchronize()
