@@ -122,6 +122,10 @@ def load_library(path: str | None = None):
                      "fdlbm_batch_moments", "fdlbm_batch_reduce", "fdlbm_batch_sync",
                      "fdlbm_batch_set_segment_rows", "fdlbm_batch_set_grid"):
             getattr(L, name).restype = ctypes.c_int
+        L.fdlbm_get_populations.argtypes = [vp, fp]
+        L.fdlbm_get_populations.restype = ctypes.c_int
+        L.fdlbm_set_populations.argtypes = [vp, fp]
+        L.fdlbm_set_populations.restype = ctypes.c_int
         L.fdlbm_walls_table_bytes.argtypes = [pp]
         L.fdlbm_walls_table_bytes.restype = ctypes.c_size_t
         L.fdlbm_set_walls.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_size_t]
@@ -253,6 +257,25 @@ class Lattice:
         """drho, ux, uy: float32 CUDA tensors [ny, nx]."""
         self._check(self.lib.fdlbm_init(self._h, self._field(drho), self._field(ux),
                                         self._field(uy)), "init")
+
+    def populations(self):
+        """MRT state (fdlbm_get_populations): a float32 CUDA tensor [9, ny, nx]
+        of f_a - w_a."""
+        import torch
+        f = torch.empty((9, self.cfg.ny, self.cfg.nx), dtype=torch.float32, device=self.device)
+        self._check(self.lib.fdlbm_get_populations(self._h, ctypes.c_void_p(f.data_ptr())),
+                    "get_populations")
+        return f
+
+    def set_populations(self, f):
+        """Replace the MRT state by f (float32 CUDA tensor [9, ny, nx], as
+        returned by populations())."""
+        import torch
+        if not (isinstance(f, torch.Tensor) and f.dtype == torch.float32 and f.is_cuda
+                and f.is_contiguous() and tuple(f.shape) == (9, self.cfg.ny, self.cfg.nx)):
+            raise ValueError("populations must be a contiguous float32 CUDA tensor [9, ny, nx]")
+        self._check(self.lib.fdlbm_set_populations(self._h, ctypes.c_void_p(f.data_ptr())),
+                    "set_populations")
 
     def set_walls(self, walls):
         """Curved walls (Sec. 3-b, fdlbm_set_walls): `walls` carries kind

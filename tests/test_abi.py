@@ -24,7 +24,7 @@ def lib():
 
 
 def test_every_declared_symbol_is_exported(lib):
-    names = _declared("fdlbm.h") + _declared("fdlbm_walls.h")
+    names = _declared("fdlbm.h") + _declared("fdlbm_walls.h") + _declared("fdlbm_populations.h")
     assert len(names) >= 17 and "fdlbm_set_walls" in names
     for n in names:
         assert hasattr(lib, n), n

@@ -58,3 +58,28 @@ def test_resume_with_curved_walls_is_exact():
     resumed = _run(cfg, _run(cfg, f, 30, walls), 40, walls)
     for a, b in zip(straight, resumed):
         assert np.array_equal(a, b)
+
+
+def test_mrt_resume_from_populations_is_exact():
+    """The MRT state is its nine populations (fdlbm_get_populations /
+    fdlbm_set_populations); resuming from them is exact, with walls and force
+    too.  The other schemes refuse the call (their state is the moments)."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    for kw in ({}, dict(boundary="walls_y", wall_xi=0.5, force=(1e-6, 0.0))):
+        cfg = F.LatticeConfig(96, 40, "mrt", s_xx=F.nu_to_s(0.02), s_e=1.5, **kw)
+        f = as_f32(inputs.random_fields(96, 40, 0.02, seed=3, rho_amp=0.01))
+        straight = _run(cfg, f, 70)
+        lat = F.Lattice(cfg)
+        lat.init(*[torch.from_numpy(np.ascontiguousarray(a)).to(lat.device) for a in f])
+        lat.step(30)
+        pops = lat.populations().clone()
+        lat2 = F.Lattice(cfg)
+        lat2.set_populations(pops)
+        lat2.step(40)
+        resumed = [t.cpu().numpy() for t in lat2.moments()]
+        for a, b in zip(straight, resumed):
+            assert np.array_equal(a, b)
+    with pytest.raises(F.FdlbmError) as e:
+        F.Lattice(F.LatticeConfig(64, 48, "fd5")).populations()
+    assert e.value.status == F.ERR_UNSUPPORTED
