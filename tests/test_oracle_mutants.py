@@ -38,6 +38,17 @@ MUTANTS = {
                       "1.0 * (vx * (dx_Pxx + dy_Pxy) - vy * (dx_Pxy + dy_Pyy))"),
 }
 
+# the nine-point stencil and the curved-wall closure, checked by their own pins
+NINE_WALL_MUTANTS = {
+    # nine points: corner weight 1/4 -> 1/2 along x
+    "fd9_corner_weight": ("                return FQ(i + 1, j) - FQ(i - 1, j) -\n                       0.25 * (",
+                          "                return FQ(i + 1, j) - FQ(i - 1, j) -\n                       0.5 * ("),
+    # curved walls: always extrapolate from the first fluid node
+    "wall_reference_node": ("const int tref = (xi >= 0.5) ? d : d + 1;", "const int tref = d;"),
+    # curved walls: density of the node along the line one step too far
+    "wall_density_node": ("    *r = F->rho[first];", "    *r = F->rho[ref];"),
+}
+
 # LW-ACM (Sec. 1-b), checked by its own pins
 LW_MUTANTS = {
     # odd part taken at the upstream node instead of the node the link points to
@@ -184,4 +195,60 @@ def test_planted_lwacm_mistake_is_caught(tmp_path, oracle_at, name):
     old, new = LW_MUTANTS[name]
     lib = _build(tmp_path, name, old, new)
     failures = _lw_pins_pass(oracle_at(lib))
+    assert failures, f"mutant {name} passed every pin"
+
+
+def _nine_wall_pins_pass(ref):
+    """Pins of the nine-point stencil (the Jacobian of one step equals the
+    symbol H(k), which Table 1 pins) and of the curved-wall closure (a
+    straight channel written as a wall table equals the channel closure,
+    whose own code the Poiseuille pins cover)."""
+    failures = []
+    p = ref.params(6, 5, 9, 1.7, 1.4)
+    X, Y = np.meshgrid(np.arange(6), np.arange(5))
+    h = 1e-6
+    for (m, n) in ((1, 0), (1, 2), (2, 1)):
+        kx, ky = 2 * np.pi * m / 6, 2 * np.pi * n / 5
+        ph = np.exp(1j * (kx * X + ky * Y))
+        B = np.zeros((3, 3), complex)
+        for c in range(3):
+            cols = []
+            for part in (ph.real, ph.imag):
+                o = []
+                for sg in (1, -1):
+                    st = [np.ones((5, 6)), np.zeros((5, 6)), np.zeros((5, 6))]
+                    st[c] = st[c] + sg * h * part
+                    o.append(np.array(ref.fd_run(p, *st, 1)))
+                cols.append((o[0] - o[1]) / (2 * h))
+            r = cols[0] + 1j * cols[1]
+            B[:, c] = (r * np.conj(ph)).mean(axis=(1, 2))
+        if np.abs(B - linear.H_fd(9, kx, ky, 1.7, 1.4)).max() > 1e-8:
+            failures.append("jacobian9")
+            break
+    nx, nyf, reach = 12, 10, 3
+    for xi in (0.25, 0.8):
+        walls = inputs.channel_walls(nx, nyf, xi, reach)
+        d, ux, uy = inputs.random_fields(nx, nyf, 0.02, seed=4, rho_amp=0.01)
+        pw = ref.params(nx, nyf, 5, 1.7, 1.4, boundary=ref.WALLS_Y, wall_xi=xi)
+        r1, x1, y1 = ref.run(pw, 1 + d, ux, uy, 10)
+        pad = lambda a, v: np.vstack([np.full((reach, nx), v), a, np.full((reach, nx), v)])
+        pp = ref.params(nx, nyf + 2 * reach, 5, 1.7, 1.4)
+        r2, x2, y2 = ref.fd_run_walls(pp, walls, pad(1 + d, 1.0), pad(ux, 0.0), pad(uy, 0.0), 10)
+        fl = slice(reach, reach + nyf)
+        if max(np.abs(r2[fl] - r1).max(), np.abs(x2[fl] - x1).max()) > 1e-14:
+            failures.append(f"channel_table_xi{xi}")
+    return failures
+
+
+def test_unmodified_oracle_passes_the_nine_point_and_wall_pins(oracle_at):
+    from oracle import ref
+    ref.build()
+    assert _nine_wall_pins_pass(oracle_at(os.path.join(ROOT, "oracle", "libfdlbm_ref.so"))) == []
+
+
+@pytest.mark.parametrize("name", sorted(NINE_WALL_MUTANTS))
+def test_planted_nine_point_or_wall_mistake_is_caught(tmp_path, oracle_at, name):
+    old, new = NINE_WALL_MUTANTS[name]
+    lib = _build(tmp_path, name, old, new)
+    failures = _nine_wall_pins_pass(oracle_at(lib))
     assert failures, f"mutant {name} passed every pin"
