@@ -216,6 +216,8 @@ size_t fdlbm_batch_workspace_size(const fdlbm_batch_params* bp);
  * fdlbm_batch_destroy; stream: a cudaStream_t. */
 int fdlbm_batch_create(const fdlbm_batch_params* bp, void* workspace, size_t workspace_bytes,
                        void* stream, fdlbm_batch_t** out);
+/* Free the batch's host state and its captured graphs; never frees the
+ * workspace (the caller's).  NULL is ignored. */
 void fdlbm_batch_destroy(fdlbm_batch_t* b);
 
 /* Reserve a slot for a lattice (p->scheme must be the batch's, storage F32);
@@ -243,8 +245,12 @@ int fdlbm_batch_sync(fdlbm_batch_t* b);
  * item (>= 8) and persistent CTAs (0 = one wave of resident CTAs). */
 int fdlbm_batch_set_segment_rows(fdlbm_batch_t* b, int32_t rows);
 int fdlbm_batch_set_grid(fdlbm_batch_t* b, int32_t ctas);
+/* Message of the batch's last failed call (owned by the batch; "NULL handle"
+ * for b == NULL). */
 const char* fdlbm_batch_last_error(const fdlbm_batch_t* b);
+/* Kernel launches the batch has enqueued since creation (-1 for NULL). */
 int64_t fdlbm_batch_launch_count(const fdlbm_batch_t* b);
+/* Number of occupied slots (-1 for NULL). */
 int32_t fdlbm_batch_count(const fdlbm_batch_t* b);
 
 /* fdlbm_reduce_fields_static -- the reductions of fdlbm_reduce for callers
@@ -297,7 +303,11 @@ int fdlbm_sync(fdlbm_t* h);
  * FDLBM_OK once enqueued, FDLBM_ERR_INVALID for tries < 0. */
 int fdlbm_selftest_wait_timeout(fdlbm_t* h, int32_t tries);
 
+/* Message of the handle's last failed call (owned by the handle, valid
+ * until its next call or destruction; "NULL handle" for h == NULL). */
 const char* fdlbm_last_error(const fdlbm_t* h);
+/* Name of a status code ("FDLBM_OK", "FDLBM_ERR_INVALID", ...; a static
+ * string, "FDLBM_UNKNOWN_STATUS" for other values). */
 const char* fdlbm_status_string(int status);
 
 /* Number of kernel launches this handle has enqueued since creation. */

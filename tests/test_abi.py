@@ -91,3 +91,41 @@ def test_no_gpu_no_lattice():
         F.Lattice(F.LatticeConfig(64, 64, "fd5"))
     with pytest.raises((RuntimeError, AssertionError, F.FdlbmError)):
         F.Batch("fd5", max_lattices=4, max_side=64, arena_bytes=1 << 20)
+
+
+_DECL = re.compile(r"^(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(fdlbm_[a-z0-9_]+)\s*\(")
+
+
+def undocumented(lines):
+    """Declarations of fdlbm_* functions not preceded by a comment.  Macros,
+    blank lines and continuation lines may sit in between; a declaration may
+    share the comment of the one before it when their names agree in their
+    first three parts (fdlbm_batch_set_grid after fdlbm_batch_set_segment_rows)."""
+    out = []
+    for i, ln in enumerate(lines):
+        m = _DECL.match(ln)
+        if not m or ln.lstrip().startswith(("*", "/*", "#")):
+            continue
+        name = m.group(1)
+        j = i - 1
+        while j >= 0:
+            prev = lines[j]
+            pm = _DECL.match(prev)
+            if prev.startswith("#define") or not prev.strip() or (
+                    prev.startswith(" ") and prev.rstrip().endswith(");")):
+                j -= 1
+            elif pm and pm.group(1).split("_")[:3] == name.split("_")[:3]:
+                j -= 1
+            else:
+                break
+        if j < 0 or not lines[j].rstrip().endswith("*/"):
+            out.append(name)
+    return out
+
+
+@pytest.mark.parametrize("header", ["fdlbm.h", "fdlbm_walls.h", "fdlbm_populations.h"])
+def test_every_declaration_is_documented(header):
+    """Each entry point of the C ABI follows a comment that states what it
+    does."""
+    lines = open(os.path.join(ROOT, "include", header)).read().split("\n")
+    assert undocumented(lines) == []
