@@ -358,6 +358,66 @@ def test_poiseuille_mrt_bounce_back(oracle):
     assert abs((-roots[0] + roots[1] - (N - 1)) / 2 - 0.5) < 0.01
 
 
+def acoustic_wall_gap(oracle, stencil, ny, nu=0.01, s_e=1.5, amp=1e-6):
+    """Distance between the acoustic walls of a channel closed at xi = 1/2,
+    minus ny.
+
+    The lowest standing sound wave between walls at y = -1/2 and
+    ny - 1/2 has u_y = 0 at both walls and, through the momentum equation,
+    a density profile cos(k (y + 1/2)) with k = pi / H, H = ny: the density
+    is even about each wall.  The run starts from exactly that profile at
+    rest, projects rho - 1 on it every step and takes the mode's rotation
+    per step omega from a two-term recurrence a(t+1) = P a(t) - Q a(t-1)
+    (Prony's method: exact for a damped cosine, omega = arg of the root of
+    z^2 - P z + Q).  The effective distance H_eff is the one for which the
+    interior dispersion relation -- the sound root of the symbol H(k)
+    (Eq. iteration, `oracle.linear`), pinned by Table 1 -- rotates by omega
+    per step."""
+    from scipy.optimize import brentq
+
+    from oracle import linear
+
+    s_xx = s_of_nu(nu)
+
+    def omega(k):
+        z = np.linalg.eigvals(linear.H_fd(stencil, 0.0, k, s_xx, s_e))
+        return float(np.max(np.abs(np.angle(z))))
+
+    nx = 4
+    prof = np.cos(np.pi / ny * (np.arange(ny) + 0.5))
+    p = oracle.params(nx, ny, stencil, s_xx, s_e, boundary=oracle.WALLS_Y, wall_xi=0.5)
+    r = 1 + amp * prof[:, None] * np.ones((1, nx))
+    x = np.zeros((ny, nx))
+    y = np.zeros((ny, nx))
+    nsteps = int(4 * 2 * np.pi / omega(np.pi / ny))  # four periods
+    a = np.zeros(nsteps)
+    for t in range(nsteps):
+        a[t] = ((r[:, 0] - 1) * prof).sum() / (prof * prof).sum()
+        r, x, y = oracle.fd_run(p, r, x, y, 1)
+    P, Q = np.linalg.lstsq(np.stack([a[1:-1], -a[:-2]], 1), a[2:], rcond=None)[0]
+    om = np.arctan2(np.sqrt(Q - P * P / 4), P / 2)
+    return brentq(lambda h: omega(np.pi / h) - om, ny - 3, ny + 3) - ny
+
+
+@pytest.mark.parametrize("stencil", [3, 5])
+def test_standing_sound_wave_between_walls(oracle, stencil):
+    """Sec. 3-b/3-c, reading R8 of the wall closure: virtual rows copy the
+    density of the first fluid row.  For a wall at xi = 1/2 that copy makes
+    rho even about y = -1/2 (row -1 equals row 0), which is where the
+    velocity closure puts the wall (u extrapolated to zero at -xi), so the
+    lowest standing sound wave fits walls at -1/2 and ny - 1/2, and the
+    closure's remaining error (rows -2, -3 also equal row 0, where the even
+    profile differs at O(k^2)) moves the walls by O(1/ny^2) only: a second-
+    order boundary condition.  Checked as H_eff - ny > 0, below 1/ny^2, and
+    (H_eff - ny) ny^2 the same at ny = 24, 48, 96 to 1 %.  A density copied
+    from the second fluid row (even about row 0) moves the walls inwards
+    (H_eff < ny) by an amount that decays more slowly than 1/ny^2."""
+    gaps = {ny: acoustic_wall_gap(oracle, stencil, ny) for ny in (24, 48, 96)}
+    scaled = np.array([g * ny * ny for ny, g in gaps.items()])
+    assert np.all(scaled > 0) and np.all(scaled < 1.0), gaps
+    assert scaled.max() / scaled.min() - 1 < 0.01, gaps
+
+
 @pytest.mark.parametrize("scheme,boundary", [(3, 0), (5, 0), (5, 1), (3, 1), (100, 0),
                                              (100, 1)])
 def test_step_points_match_full_step(oracle, scheme, boundary):

@@ -49,6 +49,20 @@ NINE_WALL_MUTANTS = {
     "wall_density_node": ("    *r = F->rho[first];", "    *r = F->rho[ref];"),
 }
 
+# the density of the channel's virtual rows, checked by the standing sound wave
+WALL_DENSITY_MUTANTS = {
+    # copied from the second fluid row instead of the first, at both walls
+    "channel_density_second_row": (
+        "        jrho = 0;\n    } else {\n        ywall = (double)(ny - 1) + xi;\n"
+        "        jref = (xi >= 0.5) ? ny - 1 : ny - 2;\n        jrho = ny - 1;",
+        "        jrho = 1;\n    } else {\n        ywall = (double)(ny - 1) + xi;\n"
+        "        jref = (xi >= 0.5) ? ny - 1 : ny - 2;\n        jrho = ny - 2;"),
+    # copied from the second fluid row at the lower wall only
+    "channel_density_second_row_lower": ("        jrho = 0;\n", "        jrho = 1;\n"),
+    # virtual rows at the rest density
+    "channel_density_at_rest": ("    *r = F->rho[(int64_t)jrho * nx + i];", "    *r = 1.0;"),
+}
+
 # LW-ACM (Sec. 1-b), checked by its own pins
 LW_MUTANTS = {
     # odd part taken at the upstream node instead of the node the link points to
@@ -251,4 +265,33 @@ def test_planted_nine_point_or_wall_mistake_is_caught(tmp_path, oracle_at, name)
     old, new = NINE_WALL_MUTANTS[name]
     lib = _build(tmp_path, name, old, new)
     failures = _nine_wall_pins_pass(oracle_at(lib))
+    assert failures, f"mutant {name} passed every pin"
+
+
+def _wall_density_pins_pass(ref):
+    """The standing sound wave between walls at xi = 1/2 (see
+    test_oracle_closed_forms.test_standing_sound_wave_between_walls): walls
+    at -1/2 and ny - 1/2 to second order, for both stencils."""
+    import test_oracle_closed_forms as C
+    failures = []
+    for stencil in (3, 5):
+        gaps = {ny: C.acoustic_wall_gap(ref, stencil, ny) for ny in (24, 48)}
+        scaled = np.array([g * ny * ny for ny, g in gaps.items()])
+        if not (np.all(scaled > 0) and np.all(scaled < 1.0)
+                and scaled.max() / scaled.min() - 1 < 0.01):
+            failures.append(f"standing_wave_fd{stencil}")
+    return failures
+
+
+def test_unmodified_oracle_passes_the_wall_density_pin(oracle_at):
+    from oracle import ref
+    ref.build()
+    assert _wall_density_pins_pass(oracle_at(os.path.join(ROOT, "oracle", "libfdlbm_ref.so"))) == []
+
+
+@pytest.mark.parametrize("name", sorted(WALL_DENSITY_MUTANTS))
+def test_planted_wall_density_mistake_is_caught(tmp_path, oracle_at, name):
+    old, new = WALL_DENSITY_MUTANTS[name]
+    lib = _build(tmp_path, name, old, new)
+    failures = _wall_density_pins_pass(oracle_at(lib))
     assert failures, f"mutant {name} passed every pin"
