@@ -100,11 +100,16 @@ extern "C" {
 /* Parameters of one lattice.  Relaxation rates lie in (0, 2).
  *   s_xx : rate of XX and XY; shear viscosity nu = (1/s_xx - 1/2)/3 (Sec. 1-a)
  *   s_e  : rate of E; bulk viscosity zeta = (1/s_e - 1/2)/3 (Sec. 1-a)
- *   s_q  : rate of qx, qy (MRT only; FD-LBM sets q = -J, Sec. 2)
+ *   s_q  : rate of qx, qy (MRT only; FD-LBM sets q = -J, Sec. 2).  For MRT,
+ *          s_q = FDLBM_S_Q_QUARTIC (0) asks the library for the rate of the
+ *          quartic condition (Eq. sigsig, Sec. 3-b): (1/s_xx - 1/2)(1/s_q - 1/2)
+ *          = 1/6, which makes the shear hyperviscosity isotropic; any other
+ *          value must lie in (0, 2).
  *   s_eps: rate of epsilon (MRT only; FD-LBM sets epsilon to equilibrium)
  *   wall_xi: walls at y = -xi and y = ny-1+xi in lattice units, 0 < xi <= 1
  *            (FD-LBM); MRT requires xi = 1/2.  Ignored when periodic.
  *   force_x, force_y: uniform body force per node and time step. */
+#define FDLBM_S_Q_QUARTIC 0.0
 typedef struct fdlbm_params {
     int32_t nx, ny;
     int32_t scheme;   /* FDLBM_SCHEME_*   */
@@ -279,6 +284,9 @@ int32_t fdlbm_batch_count(const fdlbm_batch_t* b);
  * device share the array and it keeps the last call's contents: calls
  * ordered on one stream are correct, calls that overlap on the GPU (other
  * streams, unordered host threads) race on it and give wrong results.
+ * Device: the work runs on the current CUDA device; drho, ux, uy and out
+ * must be device memory of that device (or managed memory), else the call
+ * returns FDLBM_ERR_INVALID before any work is enqueued.
  * Limits: nx, ny >= 1 and nx*ny <= FDLBM_STATIC_REDUCE_MAX_NODES; anything
  * else returns FDLBM_ERR_INVALID before any work is enqueued.  Returns
  * FDLBM_ERR_CUDA if a launch fails.  Never calls cudaMalloc or cudaFree. */

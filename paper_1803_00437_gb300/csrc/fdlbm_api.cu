@@ -38,6 +38,17 @@ static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 static bool valid_rate(double s) { return s > 0.0 && s < 2.0; }
 
+// Eq. sigsig (quartic condition, Sec. 3-b): (1/s_xx - 1/2)(1/s_q - 1/2) = 1/6.
+// For s_xx in (0, 2) the result lies in (0, 2).
+static double quartic_s_q(double s_xx) { return 1.0 / (1.0 / (6.0 * (1.0 / s_xx - 0.5)) + 0.5); }
+
+// Parameters as the kernels use them: MRT's s_q resolved from the sentinel.
+static fdlbm_params resolved_params(const fdlbm_params& p) {
+    fdlbm_params r = p;
+    if (r.scheme == FDLBM_SCHEME_MRT && r.s_q == FDLBM_S_Q_QUARTIC) r.s_q = quartic_s_q(r.s_xx);
+    return r;
+}
+
 // Parameter check shared by workspace_size and create; writes a reason.
 static int check_params(const fdlbm_params* p, char* why, size_t n) {
     auto fail = [&](int code, const char* msg) {
@@ -62,8 +73,10 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
         return fail(FDLBM_ERR_INVALID, "FDLBM_FLAG_TILED and FDLBM_FLAG_STREAM exclude each other");
     if (!valid_rate(p->s_xx) || !valid_rate(p->s_e))
         return fail(FDLBM_ERR_INVALID, "s_xx and s_e must lie in (0, 2)");
-    if (p->scheme == FDLBM_SCHEME_MRT && (!valid_rate(p->s_q) || !valid_rate(p->s_eps)))
-        return fail(FDLBM_ERR_INVALID, "MRT needs s_q and s_eps in (0, 2)");
+    if (p->scheme == FDLBM_SCHEME_MRT &&
+        ((!valid_rate(p->s_q) && p->s_q != FDLBM_S_Q_QUARTIC) || !valid_rate(p->s_eps)))
+        return fail(FDLBM_ERR_INVALID,
+                    "MRT needs s_eps in (0, 2) and s_q in (0, 2) or FDLBM_S_Q_QUARTIC");
     if (p->scheme == FDLBM_SCHEME_MRT && p->storage != FDLBM_STORAGE_F32)
         return fail(FDLBM_ERR_UNSUPPORTED, "MRT supports FP32 storage only");
     if (p->boundary == FDLBM_BOUNDARY_WALLS_Y) {
@@ -180,7 +193,7 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
     if (bytes < L.total) return FDLBM_ERR_NOMEM;
     fdlbm_t* h = new (std::nothrow) fdlbm_s();
     if (!h) return FDLBM_ERR_NOMEM;
-    h->p = *p;
+    h->p = resolved_params(*p);
     h->L = L;
     h->stream = static_cast<cudaStream_t>(stream);
     h->ws = static_cast<char*>(workspace);

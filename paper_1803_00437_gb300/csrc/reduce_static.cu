@@ -137,6 +137,19 @@ extern "C" int fdlbm_reduce_fields_static(const float* drho, const float* ux, co
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return FDLBM_ERR_CUDA;
+    // The kernels run on the current device and read the fields and write
+    // out there: each pointer must be device memory of that device (or
+    // managed memory), never host memory or another GPU's memory.
+    const void* ptrs[4] = {drho, ux, uy, out};
+    for (const void* q : ptrs) {
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, q) != cudaSuccess) {
+            cudaGetLastError();
+            return FDLBM_ERR_INVALID;
+        }
+        const bool on_dev = attr.type == cudaMemoryTypeDevice && attr.device == dev;
+        if (!on_dev && attr.type != cudaMemoryTypeManaged) return FDLBM_ERR_INVALID;
+    }
     double* partial = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_static_mutex);

@@ -26,6 +26,7 @@ STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}
 FLAG_TILED = 1
 FLAG_STREAM = 2
+S_Q_QUARTIC = 0.0
 
 
 class FdlbmError(RuntimeError):
@@ -151,11 +152,6 @@ def nu_to_s(nu: float) -> float:
     return 1.0 / (3.0 * nu + 0.5)
 
 
-def quartic_s_q(s_xx: float) -> float:
-    """Eq. sigsig: (1/s_xx - 1/2)(1/s_q - 1/2) = 1/6."""
-    return 1.0 / (1.0 / (6.0 * (1.0 / s_xx - 0.5)) + 0.5)
-
-
 @dataclass
 class LatticeConfig:
     nx: int
@@ -165,15 +161,14 @@ class LatticeConfig:
     storage: str = "f32"
     s_xx: float = 1.85
     s_e: float = 1.5
-    s_q: float | None = None
+    s_q: float | None = None  # None: FDLBM_S_Q_QUARTIC (MRT: the library applies Eq. sigsig)
     s_eps: float = 1.5
     wall_xi: float = 0.5
     force: tuple = (0.0, 0.0)
     flags: int = 0
 
     def params(self) -> Params:
-        s_q = self.s_q if self.s_q is not None else (
-            quartic_s_q(self.s_xx) if self.scheme == "mrt" else 1.0)
+        s_q = self.s_q if self.s_q is not None else S_Q_QUARTIC
         return Params(int(self.nx), int(self.ny), SCHEMES[self.scheme],
                       BOUNDARIES[self.boundary], STORAGES[self.storage], int(self.flags),
                       float(self.s_xx), float(self.s_e), float(s_q), float(self.s_eps),
@@ -394,11 +389,12 @@ def reduce_fields_static(drho, ux, uy, what: str, args=None, out=None, stream=No
         out = torch.empty(4, dtype=torch.float64, device=drho.device)
     a = None if args is None else np.ascontiguousarray(args, dtype=np.float64)
     s = stream if stream is not None else torch.cuda.current_stream(drho.device)
-    rc = lib.fdlbm_reduce_fields_static(
-        ctypes.c_void_p(drho.data_ptr()), ctypes.c_void_p(ux.data_ptr()),
-        ctypes.c_void_p(uy.data_ptr()), int(nx), int(ny), REDUCE[what],
-        ctypes.c_void_p(a.ctypes.data) if a is not None else None,
-        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    with torch.cuda.device(drho.device):  # the library works on the current device
+        rc = lib.fdlbm_reduce_fields_static(
+            ctypes.c_void_p(drho.data_ptr()), ctypes.c_void_p(ux.data_ptr()),
+            ctypes.c_void_p(uy.data_ptr()), int(nx), int(ny), REDUCE[what],
+            ctypes.c_void_p(a.ctypes.data) if a is not None else None,
+            ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
     if rc != OK:
         raise FdlbmError(rc, f"fdlbm_reduce_fields_static({what}): {status_string(rc)}")
     return out

@@ -25,8 +25,14 @@ def gpu_run(cfg, fields32, nsteps, stream=None):
     return out, lat
 
 
+def quartic_s_q(s_xx):
+    """Eq. sigsig (Sec. 3-b): (1/s_xx - 1/2)(1/s_q - 1/2) = 1/6, the rate the
+    library takes for MRT when s_q is left to it (FDLBM_S_Q_QUARTIC)."""
+    return 1.0 / (1.0 / (6.0 * (1.0 / s_xx - 0.5)) + 0.5)
+
+
 def oracle_params(oracle, cfg):
-    s_q = cfg.params().s_q
+    s_q = cfg.s_q if cfg.s_q is not None else quartic_s_q(cfg.s_xx)
     return oracle.params(cfg.nx, cfg.ny, SCHEME_TO_ORACLE[cfg.scheme], cfg.s_xx, cfg.s_e, s_q,
                          cfg.s_eps, boundary=BOUNDARY_TO_ORACLE[cfg.boundary],
                          wall_xi=cfg.wall_xi, force=cfg.force)

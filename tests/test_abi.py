@@ -129,3 +129,15 @@ def test_every_declaration_is_documented(header):
     does."""
     lines = open(os.path.join(ROOT, "include", header)).read().split("\n")
     assert undocumented(lines) == []
+
+
+def test_mrt_s_q_sentinel(lib):
+    """MRT's s_q: FDLBM_S_Q_QUARTIC (0) leaves the rate to the library (the
+    quartic condition, Eq. sigsig); other values must lie in (0, 2)."""
+    from paper_1803_00437_gb300 import fdlbm as F
+    assert F.S_Q_QUARTIC == 0.0
+    assert F.workspace_size(F.LatticeConfig(64, 48, "mrt")) > 0  # s_q None -> sentinel
+    assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", s_q=0.0)) > 0
+    assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", s_q=1.2)) > 0
+    for bad in (-0.5, 2.0, 2.5):
+        assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", s_q=bad)) == 0, bad

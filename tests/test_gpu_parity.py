@@ -235,6 +235,21 @@ def test_sound_wave_in_mean_flow(oracle, scheme):
     assert max_err(gpu, ref, amplitude(f)) <= TOL32
 
 
+def test_mrt_quartic_s_q_left_to_the_library(oracle):
+    """MRT with s_q left to the library (FDLBM_S_Q_QUARTIC) runs with the
+    rate of the quartic condition (Eq. sigsig): the same bits as passing that
+    rate, and the oracle with it within the FP32 bound."""
+    from parity_util import quartic_s_q
+    f = as_f32(inputs.random_fields(48, 40, 0.01, seed=31, rho_amp=1e-3))
+    s_xx = _nu(1 / np.sqrt(108))
+    lib_rate, _ = gpu_run(_cfg(48, 40, "mrt", s_xx=s_xx, s_e=1.5), f, 200)
+    given, _ = gpu_run(_cfg(48, 40, "mrt", s_xx=s_xx, s_e=1.5, s_q=quartic_s_q(s_xx)), f, 200)
+    for a, b in zip(lib_rate, given):
+        assert np.array_equal(a, b)
+    ref = oracle_run(oracle, _cfg(48, 40, "mrt", s_xx=s_xx, s_e=1.5), f, 200)
+    assert max_err(lib_rate, ref, amplitude(f)) <= TOL32
+
+
 def test_zero_steps_returns_initial_state(oracle):
     f = as_f32(inputs.random_fields(24, 20, 0.02, seed=1, rho_amp=0.01))
     for scheme in ("fd3", "fd5"):

@@ -79,3 +79,52 @@ def test_static_reduce_rejects_oversized_and_bad_arguments(lattice):
     assert lib.fdlbm_reduce_fields_static(*p, 0, 4, 0, None, out, None) == F.ERR_INVALID
     assert lib.fdlbm_reduce_fields_static(*p, 264, 200, 9, None, out, None) == F.ERR_INVALID
     assert lib.fdlbm_reduce_fields_static(*p, 264, 200, 3, None, out, None) == F.ERR_INVALID
+
+
+def test_static_reduce_after_a_larger_call(lattice):
+    """Every call shares the library's partial-sum array and it keeps the
+    last call's contents: a small lattice reduced after a large one (which
+    filled all 1024 blocks' partials) must read only its own partials."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F, inputs
+    big = [torch.from_numpy(np.asarray(a, dtype=np.float32)).cuda()
+           for a in inputs.random_fields(640, 512, 0.3, seed=23, rho_amp=0.5)]
+    small_np = [np.asarray(a, dtype=np.float64)
+                for a in inputs.random_fields(40, 40, 0.02, seed=24, rho_amp=0.01)]
+    small = [torch.from_numpy(a.astype(np.float32)).cuda() for a in small_np]
+    d, ux, uy = (a.astype(np.float32).astype(np.float64) for a in small_np)
+    rho = 1.0 + d
+    expect = {"mass": [d.sum()], "momentum": [(rho * ux).sum(), (rho * uy).sum()],
+              "energy": [(0.5 * rho * (ux ** 2 + uy ** 2)).sum()],
+              "maxabs": [np.hypot(ux, uy).max(), np.abs(d).max()]}
+    mags = {"mass": np.abs(d).sum(), "momentum": (rho * (np.abs(ux) + np.abs(uy))).sum(),
+            "energy": expect["energy"][0], "maxabs": 0.0}
+    for what, ref in expect.items():
+        F.reduce_fields_static(*big, what)  # 640 x 512 nodes fill every block
+        out = F.reduce_fields_static(*small, what).cpu().numpy()
+        torch.cuda.synchronize()
+        assert out[3] == 0.0
+        assert _same(out[:len(ref)], np.array(ref), mags[what]), (what, out, ref)
+
+
+def test_static_reduce_rejects_memory_off_the_device(lattice):
+    """Pointers that are not memory of the current device (here page-locked
+    host memory) are rejected before anything is enqueued."""
+    import ctypes
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    lib = F.load_library()
+    lat, fields, _ = lattice
+    host = torch.zeros(264 * 200, dtype=torch.float32).pin_memory()
+    dev = [ctypes.c_void_p(t.data_ptr()) for t in fields]
+    hp = ctypes.c_void_p(host.data_ptr())
+    out_dev = torch.zeros(4, dtype=torch.float64, device=fields[0].device)
+    od = ctypes.c_void_p(out_dev.data_ptr())
+    assert lib.fdlbm_reduce_fields_static(hp, dev[1], dev[2], 264, 200, 0, None, od,
+                                          None) == F.ERR_INVALID
+    out_host = torch.zeros(4, dtype=torch.float64).pin_memory()
+    assert lib.fdlbm_reduce_fields_static(*dev, 264, 200, 0, None,
+                                          ctypes.c_void_p(out_host.data_ptr()),
+                                          None) == F.ERR_INVALID
+    torch.cuda.synchronize()
+    assert np.all(out_host.numpy() == 0.0) and np.all(out_dev.cpu().numpy() == 0.0)
