@@ -57,6 +57,9 @@ def parse_args():
                     help="throughput: the 8192^2 headline line (default); batched: 4096 "
                          "lattices of sides 32..512; serving: the request stream")
     ap.add_argument("--lattices", type=int, default=4096, help=argparse.SUPPRESS)
+    ap.add_argument("--batched-lattices", type=int, default=1024,
+                    help="lattices of the batched sample in the default line")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -374,6 +377,14 @@ def run_ours(args):
                "unit": "MLUPS", "h2d_bytes_per_step": 3 * 4 * nodes,
                "d2h_bytes_per_step": 4 * 8, "steps": e2e_steps}
 
+    # batched lattices beside the headline lattice (a sample of the batched
+    # workload, timed the same way), one per rank
+    batched = None
+    if not args.no_batched:
+        batched = measure_batched(args.batched_lattices, min(args.steps, 50), max(args.warmup, 3),
+                                  local)
+        batched["value"] = round(all_sum(batched["value"], world, dev), 1)
+
     peak, peak_kind = hbm_peak()
 
     def roofline(scheme, kernel):
@@ -403,9 +414,15 @@ def run_ours(args):
         "fd_over_mrt_speedup": round(mrt_ms / fd_ms, 3),
         "lwacm": {"value": round(lw_value, 1), "unit": "MLUPS",
                   "ms_per_step": round(lw_ms, 5), "roofline": roofline("lwacm", "lwacm_step")},
-        "gpu_launches": int(sum(r["launches"] for r in results.values())),
+        "gpu_launches": int(sum(r["launches"] for r in results.values())
+                            + (batched["gpu_launches"] if batched else 0)),
         "clocks": clocks, "health": health, "e2e": e2e,
     }
+    if batched:
+        batched["workload"] = (f"{batched['lattices']} periodic lattices of the batched workload "
+                               "(sides U{32..512}, nu U[0.002,0.1], one transverse mode A=1e-3 "
+                               "each), FD-LBM five-point FP32, graph-captured runs")
+        line["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, rows, steps, cores = time_oracle("fd5", side, 15.0)
         line["cpu_baseline"] = {
@@ -467,56 +484,74 @@ def batch_arena_bytes(sides, strip=120, ghost=8, align=32):
     return total
 
 
-def run_batched(args):
-    """4096 independent periodic lattices, sides ~ U{32..512}, nu ~ U[0.002, 0.1],
-    each one seeded transverse mode of amplitude 1e-3, FD-LBM five-point FP32,
-    advanced together by the batched kernel in graph-captured runs."""
+def measure_batched(n_lattices: int, steps: int, warmup: int, dev_index: int = 0):
+    """The batched workload: n periodic lattices, sides ~ U{32..512}, nu ~
+    U[0.002, 0.1], each one seeded transverse mode of amplitude 1e-3, FD-LBM
+    five-point FP32, advanced together by the batched kernel in
+    graph-captured runs (rows per item chosen by the autotuner).  Returns a
+    dict: useful MLUPS, ms per step, roofline against 24 B per useful node,
+    launches and clocks of the timed region."""
     import torch
-    from paper_1803_00437_gb300 import build as B
-    B.build()
     from paper_1803_00437_gb300 import fdlbm as F
     from paper_1803_00437_gb300 import inputs
-    torch.cuda.set_device(0)
-    lats = inputs.batch_lattices(args.lattices, inputs.seed_for(2))
+    lats = inputs.batch_lattices(n_lattices, inputs.seed_for(2))
     sides = [L for L, _, _ in lats]
     nodes = sum(L * L for L in sides)
     arena = int(batch_arena_bytes(sides) * 1.02) + (1 << 20)
-    b = F.Batch("fd5", max_lattices=len(lats), arena_bytes=arena, max_side=512)
+    dev = torch.device("cuda", dev_index)
+    b = F.Batch("fd5", max_lattices=len(lats), arena_bytes=arena, max_side=512, device=dev)
     slots = [b.add(F.LatticeConfig(L, L, "fd5", s_xx=F.nu_to_s(nu), s_e=S_E)) for L, nu, _ in lats]
     seg = b.tune(steps=4)
     for s, (L, nu, md) in zip(slots, lats):
         b.init_modes(s, [md])
-    b.step(args.warmup)
+    b.step(warmup)
     b.sync()
     launches0 = b.launches
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(dev_index)
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(b.stream)
     b.sync()
     clocks = sampler.stop()
-    launches = b.launches - launches0
     ms = e0.elapsed_time(e1)
     peak, peak_kind = hbm_peak()
-    gbs = 24 * nodes * args.steps / (ms / 1e3) / 1e9
+    gbs = 24 * nodes * steps / (ms / 1e3) / 1e9
     maxu = max(float(b.reduce(s, "maxabs")[0]) for s in slots[:64])
+    out = {"value": round(nodes * steps / ms / 1e3, 1), "unit": "MLUPS", "steps": steps,
+           "warmup": warmup, "ms_per_step": round(ms / steps, 4), "lattices": len(lats),
+           "total_nodes": nodes, "rows_per_item": seg,
+           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
+                        "peak_spec": SPEC_HBM_GBS, "frac_spec": round(gbs / SPEC_HBM_GBS, 4),
+                        "traffic": None},
+           "gpu_launches": int(b.launches - launches0), "clocks": clocks,
+           "health": {"max_u_first_64": maxu}}
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    """bench.py --workload batched: 4096 lattices (the batched workload)."""
+    import torch
+    from paper_1803_00437_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    r = measure_batched(args.lattices, args.steps, args.warmup)
     line = {
-        "metric": METRIC, "workload": "batched", "value": round(nodes * args.steps / ms / 1e3, 1),
-        "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{len(lats)} periodic lattices, sides U{{32..512}}, nu U[0.002,0.1], "
-                               "one transverse mode A=1e-3 each, FD-LBM five-point FP32",
-                   "lattices": len(lats), "total_nodes": nodes, "rows_per_item": seg,
-                   "l2": "state larger than L2: no flush"},
-        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
-                     "peak_spec": SPEC_HBM_GBS, "frac_spec": round(gbs / SPEC_HBM_GBS, 4),
-                     "traffic": None},
-        "gpu_launches": int(launches), "clocks": clocks,
-        "health": {"max_u_first_64": maxu},
+        "metric": METRIC, "workload": "batched", "value": r["value"], "unit": "MLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{r['lattices']} periodic lattices, sides U{{32..512}}, nu "
+                               "U[0.002,0.1], one transverse mode A=1e-3 each, FD-LBM five-point "
+                               "FP32", "lattices": r["lattices"], "total_nodes": r["total_nodes"],
+                   "rows_per_item": r["rows_per_item"], "l2": "state larger than L2: no flush"},
+        "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        "health": r["health"],
     }
     print(json.dumps(line), flush=True)
 

@@ -36,7 +36,9 @@
  *     fdlbm_status.  Nothing aborts or throws.  The text of the last error on
  *     a handle is available from fdlbm_last_error.  A device-side wait that
  *     ran out (FDLBM_ERR_TIMEOUT) is reported by the next fdlbm_sync or
- *     fdlbm_reduce; non-finite values by fdlbm_reduce (FDLBM_ERR_DIVERGED).
+ *     fdlbm_reduce; non-finite values by fdlbm_reduce (FDLBM_ERR_DIVERGED);
+ *     a saturated fixed-point store (FDLBM_ERR_RANGE) by fdlbm_sync or
+ *     fdlbm_reduce.
  *   - A handle may be used by one host thread at a time.
  */
 #ifndef FDLBM_H
@@ -57,6 +59,8 @@ extern "C" {
 #define FDLBM_ERR_CUDA (-4)        /* a CUDA runtime call failed            */
 #define FDLBM_ERR_DIVERGED (-5)    /* non-finite values found on the device */
 #define FDLBM_ERR_TIMEOUT (-6)     /* a bounded device-side wait expired    */
+#define FDLBM_ERR_RANGE (-7)       /* a value beyond storage_range (I16 storage)
+                                      was stored saturated                   */
 
 /* ---- scheme, boundary, storage ----------------------------------------- */
 #define FDLBM_SCHEME_FD3 3   /* FD-LBM, three-point differences (Sec. 2)   */
@@ -84,6 +88,17 @@ extern "C" {
 #define FDLBM_STORAGE_F32 0  /* state stored in FP32                      */
 #define FDLBM_STORAGE_F16 1  /* FD-LBM only: (rho-1, ux, uy) in FP16, FP32 math */
 #define FDLBM_STORAGE_BF16 2 /* FD-LBM only: (rho-1, ux, uy) in BF16, FP32 math */
+/* FD-LBM only: (rho-1, ux, uy) in 16-bit fixed point, FP32 math.  A value v
+ * is stored as q = round_to_nearest(v * 32767 / storage_range), |q| <= 32767,
+ * and read as q * storage_range / 32767: a uniform spacing of
+ * storage_range / 32767 instead of FP16's 2^-11 relative spacing, which the
+ * slow per-step change of the fields (nu k^2 of their value) needs.  A value
+ * beyond +-storage_range (or not finite) is stored saturated at the bound and
+ * reported as FDLBM_ERR_RANGE by the next fdlbm_sync or fdlbm_reduce; the
+ * caller chooses storage_range above the largest |rho - 1|, |ux|, |uy| the
+ * flow will reach.  Curved walls (fdlbm_set_walls) are not supported with
+ * it. */
+#define FDLBM_STORAGE_I16 3
 
 /* Kernel choice for FD-LBM lattices.  By default a lattice that qualifies
  * for the streaming kernel (periodic or channel, nx % 8 == 0, nx >= 256,
@@ -108,7 +123,9 @@ extern "C" {
  *   s_eps: rate of epsilon (MRT only; FD-LBM sets epsilon to equilibrium)
  *   wall_xi: walls at y = -xi and y = ny-1+xi in lattice units, 0 < xi <= 1
  *            (FD-LBM); MRT requires xi = 1/2.  Ignored when periodic.
- *   force_x, force_y: uniform body force per node and time step. */
+ *   force_x, force_y: uniform body force per node and time step.
+ *   storage_range: FDLBM_STORAGE_I16 only, the largest |value| representable
+ *            (> 0); ignored by the other storage types. */
 #define FDLBM_S_Q_QUARTIC 0.0
 typedef struct fdlbm_params {
     int32_t nx, ny;
@@ -119,6 +136,7 @@ typedef struct fdlbm_params {
     double s_xx, s_e, s_q, s_eps;
     double wall_xi;
     double force_x, force_y;
+    double storage_range;
 } fdlbm_params;
 
 typedef struct fdlbm_s fdlbm_t;

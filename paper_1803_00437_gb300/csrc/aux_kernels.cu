@@ -13,41 +13,45 @@ constexpr int kThreads = 256;
 template <typename T>
 __global__ void fd_init_kernel(const float* __restrict__ drho, const float* __restrict__ ux,
                                const float* __restrict__ uy, T* __restrict__ dst, int nx, int ny,
-                               size_t pitch, size_t plane) {
+                               size_t pitch, size_t plane, Quant q, int* status) {
     const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
     const size_t i = (size_t)y * nx + x, o = (size_t)y * pitch + x;
-    Storage<T>::store(dst + o, drho[i]);
-    Storage<T>::store(dst + plane + o, ux[i]);
-    Storage<T>::store(dst + 2 * plane + o, uy[i]);
+    bool sat = Storage<T>::store(dst + o, drho[i], q);
+    sat |= Storage<T>::store(dst + plane + o, ux[i], q);
+    sat |= Storage<T>::store(dst + 2 * plane + o, uy[i], q);
+    if (sat) report_saturation(status);
 }
 
 // Four consecutive columns per thread (nx % 4 == 0, sources 16-byte
 // aligned): 16-byte loads, which is what keeps the host link busy when the
 // sources are page-locked host memory read in place.
 template <typename T>
-__device__ __forceinline__ void store4(T* p, float4 v) {
-    Storage<T>::store(p, v.x);
-    Storage<T>::store(p + 1, v.y);
-    Storage<T>::store(p + 2, v.z);
-    Storage<T>::store(p + 3, v.w);
+__device__ __forceinline__ bool store4(T* p, float4 v, Quant q) {
+    bool sat = Storage<T>::store(p, v.x, q);
+    sat |= Storage<T>::store(p + 1, v.y, q);
+    sat |= Storage<T>::store(p + 2, v.z, q);
+    sat |= Storage<T>::store(p + 3, v.w, q);
+    return sat;
 }
 template <>
-__device__ __forceinline__ void store4<float>(float* p, float4 v) {
+__device__ __forceinline__ bool store4<float>(float* p, float4 v, Quant) {
     *reinterpret_cast<float4*>(p) = v;  // rows start 256-byte aligned
+    return false;
 }
 
 template <typename T>
 __global__ void fd_init_vec4_kernel(const float4* __restrict__ drho, const float4* __restrict__ ux,
                                     const float4* __restrict__ uy, T* __restrict__ dst, int nx4,
-                                    int ny, size_t pitch, size_t plane) {
+                                    int ny, size_t pitch, size_t plane, Quant q, int* status) {
     const int x4 = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
     if (x4 >= nx4) return;
     const size_t i = (size_t)y * nx4 + x4, o = (size_t)y * pitch + 4 * (size_t)x4;
     const float4 a = drho[i], b = ux[i], c = uy[i];
-    store4(dst + o, a);
-    store4(dst + plane + o, b);
-    store4(dst + 2 * plane + o, c);
+    bool sat = store4(dst + o, a, q);
+    sat |= store4(dst + plane + o, b, q);
+    sat |= store4(dst + 2 * plane + o, c, q);
+    if (sat) report_saturation(status);
 }
 
 // ---- MRT: equilibrium start --------------------------------------------------
@@ -159,11 +163,11 @@ __global__ void __launch_bounds__(kThreads)
 // ---- moments ---------------------------------------------------------------------
 
 template <typename T>
-__device__ __forceinline__ void fd_node(const T* s, size_t plane, size_t o, float* dr,
+__device__ __forceinline__ void fd_node(const T* s, size_t plane, size_t o, Quant q, float* dr,
                                         float* ux, float* uy) {
-    *dr = Storage<T>::load(s + o);
-    *ux = Storage<T>::load(s + plane + o);
-    *uy = Storage<T>::load(s + 2 * plane + o);
+    *dr = Storage<T>::load(s + o, q);
+    *ux = Storage<T>::load(s + plane + o, q);
+    *uy = Storage<T>::load(s + 2 * plane + o, q);
 }
 
 template <bool WALLS>
@@ -183,9 +187,9 @@ __device__ __forceinline__ void mrt_node(const float* s, int x, int y, int nx, i
 template <typename T, int KIND>  // KIND 0: FD-LBM, 1: MRT periodic, 2: MRT walls
 __device__ __forceinline__ void node_state(const void* s, int x, int y, int nx, int ny,
                                            size_t pitch, size_t plane, float fx, float fy,
-                                           float* dr, float* ux, float* uy) {
+                                           Quant q, float* dr, float* ux, float* uy) {
     if (KIND == 0)
-        fd_node(static_cast<const T*>(s), plane, (size_t)y * pitch + x, dr, ux, uy);
+        fd_node(static_cast<const T*>(s), plane, (size_t)y * pitch + x, q, dr, ux, uy);
     else
         mrt_node<KIND == 2>(static_cast<const float*>(s), x, y, nx, ny, pitch, plane, fx, fy,
                             dr, ux, uy);
@@ -193,12 +197,12 @@ __device__ __forceinline__ void node_state(const void* s, int x, int y, int nx, 
 
 template <typename T, int KIND>
 __global__ void moments_kernel(const void* s, int nx, int ny, size_t pitch, size_t plane,
-                               float fx, float fy, float* __restrict__ drho,
+                               float fx, float fy, Quant q, float* __restrict__ drho,
                                float* __restrict__ ux, float* __restrict__ uy) {
     const int x = blockIdx.x * kThreads + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
     float dr, vx, vy;
-    node_state<T, KIND>(s, x, y, nx, ny, pitch, plane, fx, fy, &dr, &vx, &vy);
+    node_state<T, KIND>(s, x, y, nx, ny, pitch, plane, fx, fy, q, &dr, &vx, &vy);
     const size_t i = (size_t)y * nx + x;
     drho[i] = dr;
     ux[i] = vx;
@@ -259,7 +263,7 @@ constexpr int kRowChunk = 64;
 template <typename T, int KIND, int WHAT>
 __global__ void __launch_bounds__(kThreads)
     reduce_kernel(const void* s, int nx, int ny, size_t pitch, size_t plane, float fx, float fy,
-                  double a0, double a1, double* __restrict__ partial) {
+                  Quant q, double a0, double a1, double* __restrict__ partial) {
     double acc[kReduceSlots] = {0.0, 0.0, 0.0, 0.0};
     __shared__ double2 rowph[kRowChunk];
     double kx = 0.0, ky = 0.0, tx = 0.0, ty = 0.0;
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(kThreads)
                     bdr[i] = bux[i] = buy[i] = 0.f;
                     if (r0 + i < nrows)
                         node_state<T, KIND>(s, x, y0 + r0 + i, nx, ny, pitch, plane, fx, fy,
-                                            &bdr[i], &bux[i], &buy[i]);
+                                            q, &bdr[i], &bux[i], &buy[i]);
                 }
 #pragma unroll
                 for (int i = 0; i < kBatch; ++i) {
@@ -402,55 +406,45 @@ cudaError_t dispatch_kind(fdlbm_s* h, F&& f) {
     switch (h->p.storage) {
         case FDLBM_STORAGE_F16: return f.template run<__half, 0>();
         case FDLBM_STORAGE_BF16: return f.template run<__nv_bfloat16, 0>();
+        case FDLBM_STORAGE_I16: return f.template run<int16_t, 0>();
         default: return f.template run<float, 0>();
     }
 }
 
-}  // namespace
-
-cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
-                           void* dst) {
+template <typename T>
+cudaError_t launch_fd_init_typed(fdlbm_s* h, const float* drho, const float* ux,
+                                 const float* uy, void* dst) {
+    const Quant q = quant_of(h->p);
+    int* status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
     const bool vec4 = h->p.nx % 4 == 0 &&
                       ((reinterpret_cast<uintptr_t>(drho) | reinterpret_cast<uintptr_t>(ux) |
                         reinterpret_cast<uintptr_t>(uy)) & 15) == 0;
     if (vec4) {
         const int nx4 = h->p.nx / 4;
         dim3 grid4((nx4 + kThreads - 1) / kThreads, h->p.ny);
-        const float4* a = reinterpret_cast<const float4*>(drho);
-        const float4* b = reinterpret_cast<const float4*>(ux);
-        const float4* c = reinterpret_cast<const float4*>(uy);
-        switch (h->p.storage) {
-            case FDLBM_STORAGE_F16:
-                fd_init_vec4_kernel<__half><<<grid4, kThreads, 0, h->stream>>>(
-                    a, b, c, static_cast<__half*>(dst), nx4, h->p.ny, h->L.pitch, h->L.plane);
-                break;
-            case FDLBM_STORAGE_BF16:
-                fd_init_vec4_kernel<__nv_bfloat16><<<grid4, kThreads, 0, h->stream>>>(
-                    a, b, c, static_cast<__nv_bfloat16*>(dst), nx4, h->p.ny, h->L.pitch,
-                    h->L.plane);
-                break;
-            default:
-                fd_init_vec4_kernel<float><<<grid4, kThreads, 0, h->stream>>>(
-                    a, b, c, static_cast<float*>(dst), nx4, h->p.ny, h->L.pitch, h->L.plane);
-        }
+        fd_init_vec4_kernel<T><<<grid4, kThreads, 0, h->stream>>>(
+            reinterpret_cast<const float4*>(drho), reinterpret_cast<const float4*>(ux),
+            reinterpret_cast<const float4*>(uy), static_cast<T*>(dst), nx4, h->p.ny,
+            h->L.pitch, h->L.plane, q, status);
         return cudaGetLastError();
     }
     dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
-    switch (h->p.storage) {
-        case FDLBM_STORAGE_F16:
-            fd_init_kernel<__half><<<grid, kThreads, 0, h->stream>>>(
-                drho, ux, uy, static_cast<__half*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane);
-            break;
-        case FDLBM_STORAGE_BF16:
-            fd_init_kernel<__nv_bfloat16><<<grid, kThreads, 0, h->stream>>>(
-                drho, ux, uy, static_cast<__nv_bfloat16*>(dst), h->p.nx, h->p.ny, h->L.pitch,
-                h->L.plane);
-            break;
-        default:
-            fd_init_kernel<float><<<grid, kThreads, 0, h->stream>>>(
-                drho, ux, uy, static_cast<float*>(dst), h->p.nx, h->p.ny, h->L.pitch, h->L.plane);
-    }
+    fd_init_kernel<T><<<grid, kThreads, 0, h->stream>>>(drho, ux, uy, static_cast<T*>(dst),
+                                                        h->p.nx, h->p.ny, h->L.pitch,
+                                                        h->L.plane, q, status);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
+                           void* dst) {
+    switch (h->p.storage) {
+        case FDLBM_STORAGE_F16: return launch_fd_init_typed<__half>(h, drho, ux, uy, dst);
+        case FDLBM_STORAGE_BF16: return launch_fd_init_typed<__nv_bfloat16>(h, drho, ux, uy, dst);
+        case FDLBM_STORAGE_I16: return launch_fd_init_typed<int16_t>(h, drho, ux, uy, dst);
+        default: return launch_fd_init_typed<float>(h, drho, ux, uy, dst);
+    }
 }
 
 cudaError_t launch_mrt_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
@@ -489,7 +483,7 @@ struct MomentsLaunch {
         dim3 grid((h->p.nx + kThreads - 1) / kThreads, h->p.ny);
         moments_kernel<T, KIND><<<grid, kThreads, 0, h->stream>>>(
             s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
-            (float)h->p.force_y, dr, ux, uy);
+            (float)h->p.force_y, quant_of(h->p), dr, ux, uy);
         return cudaGetLastError();
     }
 };
@@ -512,7 +506,7 @@ struct ReduceLaunch {
     cudaError_t go() {
         reduce_kernel<T, KIND, WHAT><<<reduce_grid(h->p.nx, h->p.ny), kThreads, 0, h->stream>>>(
             s, h->p.nx, h->p.ny, h->L.pitch, h->L.plane, (float)h->p.force_x,
-            (float)h->p.force_y, a0, a1, partial);
+            (float)h->p.force_y, quant_of(h->p), a0, a1, partial);
         return cudaGetLastError();
     }
     template <typename T, int KIND>

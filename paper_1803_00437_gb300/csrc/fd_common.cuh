@@ -118,20 +118,20 @@ __device__ __forceinline__ void fd_close(const float p[9], const FdCoeffs& c, fl
 // second), rho - 1 copied from the first fluid row (Sec. 3-b, 3-c).
 template <bool WALLS, typename T>
 __device__ __forceinline__ void fd_load_node(const FdState<T>& s, int x, int y, int ny,
-                                             size_t pitch, float xi, float* dr, float* ux,
-                                             float* uy) {
+                                             size_t pitch, float xi, Quant q, float* dr,
+                                             float* ux, float* uy) {
     if (!WALLS) {
         const size_t o = (size_t)wrap_index(y, ny) * pitch + x;
-        *dr = Storage<T>::load(s.drho + o);
-        *ux = Storage<T>::load(s.ux + o);
-        *uy = Storage<T>::load(s.uy + o);
+        *dr = Storage<T>::load(s.drho + o, q);
+        *ux = Storage<T>::load(s.ux + o, q);
+        *uy = Storage<T>::load(s.uy + o, q);
         return;
     }
     if (y >= 0 && y < ny) {
         const size_t o = (size_t)y * pitch + x;
-        *dr = Storage<T>::load(s.drho + o);
-        *ux = Storage<T>::load(s.ux + o);
-        *uy = Storage<T>::load(s.uy + o);
+        *dr = Storage<T>::load(s.drho + o, q);
+        *ux = Storage<T>::load(s.ux + o, q);
+        *uy = Storage<T>::load(s.uy + o, q);
         return;
     }
     const bool below = y < 0;
@@ -140,9 +140,9 @@ __device__ __forceinline__ void fd_load_node(const FdState<T>& s, int x, int y, 
     const float ywall = below ? -xi : (float)(ny - 1) + xi;
     const float factor = ((float)y - ywall) / ((float)jref - ywall);
     const size_t oe = (size_t)edge * pitch + x, orf = (size_t)jref * pitch + x;
-    *dr = Storage<T>::load(s.drho + oe);
-    *ux = Storage<T>::load(s.ux + orf) * factor;
-    *uy = Storage<T>::load(s.uy + orf) * factor;
+    *dr = Storage<T>::load(s.drho + oe, q);
+    *ux = Storage<T>::load(s.ux + orf, q) * factor;
+    *uy = Storage<T>::load(s.uy + orf, q) * factor;
 }
 
 }  // namespace fdlbm

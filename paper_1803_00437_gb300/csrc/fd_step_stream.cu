@@ -1,27 +1,33 @@
 // fd_step_stream.cu -- FD-LBM step (Sec. 2, Eq. 2) for lattices periodic in
-// x (periodic or walled in y), streaming each warp down a strip of rows.
+// x (periodic or walled in y), streaming each CTA down a strip of rows.
 //
-// Work decomposition.  A warp owns an output strip of 120 columns and a
-// segment of rows.  Lane L holds 4 consecutive columns starting at
-// strip0 - 4 + 4 L, so lanes 0 and 31 are halo lanes: they reconstruct the
-// populations one column outside the strip (where the gradients they need
-// are still exact) and store nothing.  Warps never synchronise with each
-// other.
+// Work decomposition.  A CTA of W = 2 warps owns an output strip of W x 120
+// columns and a segment of rows; warp w owns the 120 columns from w x 120.  Lane L of a warp holds 4 consecutive columns
+// starting at 4 L - 4 of the warp's strip, so lanes 0 and 31 are halo lanes:
+// they reconstruct the populations one column outside the warp's strip
+// (where the gradients they need are still exact) and store nothing.
 //
-// Data path per warp.  Rows of (rho - 1, ux, uy) for the strip plus 8 halo
-// columns are copied by 1-D bulk (TMA) copies into a private ring of 8
-// shared-memory slots, each completed by an mbarrier, several rows ahead of
-// use (two rows per issue, six lanes issuing one copy each).  Each lane
-// reads its 4 columns (one 16-byte load per field for FP32).  Derivatives
-// along y: three points hold the two previous rows in registers; five points
-// hold only the (negated) differences d1(c) = f(c+1) - f(c-1) and use
-// 8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), the centre row being re-read from the
-// ring.  Derivatives along x use warp shuffles of the two neighbouring
-// columns on each side.  Arithmetic on column pairs uses the paired FP32
-// instructions of sm_100-family GPUs.  After the reconstruction the
-// populations that cross a lane boundary are exchanged by shuffles, summed
-// per destination row and closed when the row below has contributed.
+// Data path.  Rows of (rho - 1, ux, uy) for the CTA strip plus 8 halo
+// columns on each side are copied by 1-D bulk (TMA) copies -- one per field
+// and row for the whole CTA, two where the row wraps around x -- into a ring
+// of 8 shared-memory row slots, each completed by an mbarrier, several rows
+// ahead of use.  Every warp releases a slot once it has read the slot's row
+// for the last time (the row is then the centre row of the derivative
+// window); the warp whose release is the slot's last (a shared-memory
+// counter, atomic with acquire-release order) refills it with the row
+// eight positions ahead.  Warps therefore never wait for each other, only
+// for copies.  Each lane reads its 4 columns (one 16-byte load per field for
+// FP32).  Derivatives along y: three points hold the two previous rows in
+// registers; five points hold only the (negated) differences
+// d1(c) = f(c+1) - f(c-1) and use 8 d/dy = 6 d1(c) - d1(c-1) - d1(c+1), the
+// centre row being re-read from the ring.  Derivatives along x use warp
+// shuffles of the two neighbouring columns on each side.  Arithmetic on
+// column pairs uses the paired FP32 instructions of sm_100-family GPUs.
+// After the reconstruction the populations that cross a lane boundary are
+// exchanged by shuffles, summed per destination row and closed when the row
+// below has contributed.
 #include <algorithm>
+#include <type_traits>
 
 #include "fd_stream_common.cuh"
 #include "tma_ring.cuh"
@@ -31,23 +37,26 @@ namespace {
 
 using namespace stream;
 
-constexpr int kWarpsPerBlock = 1;
 constexpr int kStrip = 120;     // output columns per warp
-constexpr int kLoadCols = 136;  // columns staged per row: strip0 - 8 .. strip0 + 128
+constexpr int kHalo = 8;        // staged columns on each side of a CTA strip
 constexpr int kSlots = 8;       // ring depth (rows); a power of two
 constexpr int kSlotMask = kSlots - 1;
+// Resident warps per SM the launch bounds aim at: 128 registers per thread
+// (8 CTAs of 2 warps), the register file's limit at that count.
+constexpr int kWarpsPerSM = 16;
 
-// One warp per CTA (warps never synchronise), 16 resident per SM: the
-// register allocator then fits the step in 128 registers without spills and
-// occupancy is set by registers and shared memory (16 x 13 KB rings), not by
-// CTA granularity.  Measured on GB300: 16 one-warp CTAs beat 3 four-warp CTAs
-// (168 registers) by 6 %.
-#ifndef FDLBM_STREAM_MIN_BLOCKS
-#define FDLBM_STREAM_MIN_BLOCKS 16
-#endif
-template <int R>
-constexpr int min_blocks() {
-    return FDLBM_STREAM_MIN_BLOCKS;
+// Columns staged per row for a CTA of W warps.  W x 120 + 16 elements are a
+// multiple of 16 bytes in every storage type.
+__host__ __device__ constexpr int load_cols(int W) { return W * kStrip + 2 * kHalo; }
+
+// Shared memory of a CTA: the ring (kSlots x 3 fields x load_cols), then
+// kSlots completion barriers, kSlots release counters and kSlots records of
+// the last ring position issued to each slot.
+__host__ __device__ constexpr size_t ring_bytes(int W, int elem) {
+    return (size_t)kSlots * 3 * load_cols(W) * elem;
+}
+__host__ __device__ constexpr size_t smem_bytes(int W, int elem) {
+    return ring_bytes(W, elem) + kSlots * (8 + 4 + 4);
 }
 
 struct StreamArgs {
@@ -57,34 +66,39 @@ struct StreamArgs {
     size_t pitch;     // elements per row
     int nx, ny;
     float xi;         // wall offset (channels)
-    int nstrips, seg_rows, nsegs, nitems;
+    int nstrips;      // warp strips of 120 columns
+    int ncstrips;     // CTA strips (W warp strips each, the last maybe fewer)
+    int seg_rows, nsegs, nitems;
     StreamCoeffs k;
+    Quant q;          // fixed-point scale (FDLBM_STORAGE_I16)
     int* status;      // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
 };
 
-template <typename T>
-struct Ring {
-    T* slot_base;    // kSlots x 3 x kLoadCols elements
-    uint64_t* bars;  // kSlots barriers
+// Per-item constants, uniform over the CTA.
+struct Item {
+    int strip0;        // first output column of the CTA strip
+    int active;        // warps of the CTA with columns in this strip
+    int yb, ye;        // output rows [yb, ye)
+    int row_first;     // lattice row of ring row 0 (yb - 1 - R)
+    int nrows;         // rows streamed: ye - yb + 2 + 2R
+    int x0, first;     // staged columns: load_cols from x0, wrapping once at nx
 };
 
-template <typename T>
-__device__ __forceinline__ T* slot_field(const Ring<T>& ring, int slot, int field) {
-    return ring.slot_base + (slot * 3 + field) * kLoadCols;
+template <int R>
+__device__ __forceinline__ Item make_item(const StreamArgs& a, int item, int W) {
+    Item it;
+    const int cs = item % a.ncstrips, seg = item / a.ncstrips;
+    it.strip0 = cs * W * kStrip;
+    it.active = min(W, a.nstrips - cs * W);
+    it.yb = seg * a.seg_rows;
+    it.ye = min(a.ny, it.yb + a.seg_rows);
+    it.row_first = it.yb - 1 - R;
+    it.nrows = it.ye - it.yb + 2 + 2 * R;
+    it.x0 = wrap_index(it.strip0 - kHalo, a.nx);
+    it.first = min(load_cols(W), a.nx - it.x0);
+    return it;
 }
 
-// Per-item constants of a warp.
-struct Item {
-    int strip0, yb, ye, row_first, nrows;
-    int x0, first;     // staged columns: kLoadCols from x0, wrapping once at nx
-    bool lane_stores;  // this lane's 4 columns are output columns
-    uint32_t base;     // ring position of the item's row 0
-    size_t out;        // element offset of this lane's columns in output row yb
-};
-
-// Issue rows k0 .. k0 + count - 1 (count 1 or 2) of the item into their ring
-// slots: lanes 0..count-1 first arm the rows' barriers with the byte count,
-// then lanes 0..3 count - 1 each copy one field of one row.
 // Channel (walls in y): a row outside [0, ny) is virtual (Sec. 3-b, 3-c
 // closure): its rho - 1 is the first fluid row's and its u the reference
 // row's (the first fluid row if xi >= 1/2, else the second) times the linear
@@ -99,34 +113,57 @@ __device__ __forceinline__ float wall_factor(int r, int ny, float xi) {
     return ((float)r - ywall) / ((float)wall_ref(r, ny, xi) - ywall);
 }
 
-template <bool WALLS, typename T>
-__device__ __forceinline__ void issue_rows(const StreamArgs& a, const Ring<T>& ring,
-                                           const Item& it, int k0, int count, int lane) {
-    if (lane < count) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&ring.bars[(it.base + k0 + lane) & kSlotMask],
-                              3u * kLoadCols * sizeof(T));
+// The ring lives at the start of the dynamic shared memory; its barriers,
+// counters and records follow it.  Only 32-bit offsets are kept.
+extern __shared__ __align__(128) unsigned char g_smem[];
+
+template <int W, typename T>
+struct Ring {
+    static constexpr uint32_t cols = load_cols(W);  // staged columns per row
+    static constexpr uint32_t field_bytes = cols * sizeof(T);
+    static constexpr uint32_t slot_bytes = 3 * field_bytes;
+    static constexpr uint32_t tail = kSlots * slot_bytes;  // barriers, counters, records
+    static __device__ __forceinline__ uint64_t* full(int slot) {
+        return reinterpret_cast<uint64_t*>(g_smem + tail) + slot;
     }
-    __syncwarp();
-    if (lane < 3 * count) {
-        const int j = lane >= 3 ? 1 : 0;  // which row this lane copies
-        const int f = lane - 3 * j;       // which field
-        const int slot = (it.base + k0 + j) & kSlotMask;
-        int r = it.row_first + k0 + j;
-        if (!WALLS) {
-            if (r < 0) r += a.ny;
-            if (r >= a.ny) r -= a.ny;
-        } else if (r < 0 || r >= a.ny) {
-            r = f == 0 ? wall_edge(r, a.ny) : wall_ref(r, a.ny, a.xi);
-        }
-        fence_proxy_async_smem();
-        const T* rowp = static_cast<const T*>(a.src) + f * a.plane + (size_t)r * a.pitch;
-        T* dst = slot_field(ring, slot, f);
-        uint64_t* bar = &ring.bars[slot];
-        tma_load_1d(dst, rowp + it.x0, it.first * sizeof(T), bar);
-        if (it.first < kLoadCols)
-            tma_load_1d(dst + it.first, rowp, (kLoadCols - it.first) * sizeof(T), bar);
+    static __device__ __forceinline__ uint32_t* count(int slot) {
+        return reinterpret_cast<uint32_t*>(g_smem + tail + kSlots * 8) + slot;
     }
+    static __device__ __forceinline__ int* last(int slot) {
+        return reinterpret_cast<int*>(g_smem + tail + kSlots * 12) + slot;
+    }
+};
+
+// Copy ring row k of the item (ring position pos) into its slot; one thread.
+template <bool WALLS, typename T, int W>
+__device__ __forceinline__ void issue_row(const StreamArgs& a, const Item& it, uint32_t pos,
+                                          int k) {
+    using ring = Ring<W, T>;
+    const int slot = pos & kSlotMask;
+    uint64_t* bar = ring::full(slot);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, 3u * ring::cols * sizeof(T));
+    int r = it.row_first + k;
+    int rref = r;
+    if (!WALLS) {
+        if (r < 0) r += a.ny;
+        if (r >= a.ny) r -= a.ny;
+        rref = r;
+    } else if (r < 0 || r >= a.ny) {
+        rref = wall_ref(r, a.ny, a.xi);
+        r = wall_edge(r, a.ny);
+    }
+    T* dst = reinterpret_cast<T*>(g_smem) + (size_t)slot * 3 * ring::cols;
+    const T* src = static_cast<const T*>(a.src);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const T* rowp = src + f * a.plane + (size_t)(f == 0 ? r : rref) * a.pitch;
+        T* d = dst + f * ring::cols;
+        tma_load_1d(d, rowp + it.x0, it.first * sizeof(T), bar);
+        if (it.first < (int)ring::cols)
+            tma_load_1d(d + it.first, rowp, (ring::cols - it.first) * sizeof(T), bar);
+    }
+    *ring::last(slot) = (int)pos;
 }
 
 // Rows before this one are the window's warm-up: the centre row does not
@@ -136,33 +173,63 @@ __host__ __device__ constexpr int warm_rows() {
     return 2 * R + 2;
 }
 
-// Wait (bounded) for field row k of the item to land in its slot.
-template <typename T>
-__device__ __forceinline__ bool row_landed(const Ring<T>& ring, const Item& it, int k) {
-    const uint32_t pos = it.base + k;
-    return mbar_wait_bounded(&ring.bars[pos & kSlotMask], (pos / kSlots) & 1u);
+// Wait (bounded) for ring position pos to land in its slot.
+template <int W, typename T>
+__device__ __forceinline__ bool row_landed(uint32_t pos) {
+    return mbar_wait_bounded(Ring<W, T>::full(pos & kSlotMask), (pos / kSlots) & 1u);
 }
 
-template <int R, bool FORCE, bool WALLS, typename T>
+// Atomic increment of a release counter that wraps to 0 after `last`,
+// ordered (acquire-release, CTA scope) after this thread's and -- through
+// the preceding __syncwarp -- its warp's reads of the slot.
+__device__ __forceinline__ uint32_t release_inc(uint32_t* counter, uint32_t last) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.inc.u32 %0, [%1], %2;"
+                 : "=r"(old)
+                 : "r"(smem_u32(counter)), "r"(last)
+                 : "memory");
+    return old;
+}
+
+// The warp has read ring row m for the last time: count its release; the
+// CTA's last release refills the slot with row m + kSlots.  Lane 0 only;
+// the item's description is read from shared memory (it is needed only
+// here, so it is not held in registers through the row loop).
+template <bool WALLS, typename T, int W>
+__device__ __forceinline__ void release_row(const StreamArgs& a, const Item* s_item,
+                                            uint32_t base, int m) {
+    const int nrows = s_item->nrows, active = s_item->active;
+    if (m < 0 || m + kSlots >= nrows) return;  // no refill follows this row
+    const uint32_t pos = base + m;
+    if (release_inc(Ring<W, T>::count(pos & kSlotMask), active - 1) == (uint32_t)(active - 1)) {
+        const Item it = *s_item;
+        issue_row<WALLS, T, W>(a, it, pos + kSlots, m + kSlots);
+    }
+}
+
+template <int R, bool FORCE, bool WALLS, typename T, int W>
 struct RowStep {
     // Field row k of the item (already landed): read it, update the y window
-    // and reconstruct the centre row c = row k - R; close and store row c - 1.
+    // and reconstruct the centre row c = row k - R; close and store row c - 1
+    // through the running output pointer `out` (row yb + k - 2R - 2).
     // WARM: k may be below warm_rows<R>(), so the centre-row read and the
     // store are guarded; otherwise both are unconditional.
     template <bool WARM>
-    static __device__ __forceinline__ void run(const StreamArgs& a, const Ring<T>& ring,
-                                               const Item& it, int lane, int k, Win& fm2,
+    static __device__ __forceinline__ void run(const StreamArgs& a, int row_first,
+                                               uint32_t lane_off, uint32_t base, int k,
+                                               bool stores, T*& out, bool& sat, Win& fm2,
                                                Win& fm1, Win& dm3, Win& dm2, Acc& acc) {
-        const uint32_t pos = it.base + k;
-        const int slot = pos & kSlotMask;
-        const int col = 4 + 4 * lane;  // slot column of this lane's first column
+        constexpr uint32_t slot_bytes = Ring<W, T>::slot_bytes;
+        constexpr uint32_t field_bytes = Ring<W, T>::field_bytes;
+        const uint32_t pos = base + k;
+        const uint32_t row = lane_off + (pos & kSlotMask) * slot_bytes;
         float2 nr[2], nux[2], nuy[2];
-        Vec4<T>::load(slot_field(ring, slot, 0) + col, nr);
-        Vec4<T>::load(slot_field(ring, slot, 1) + col, nux);
-        Vec4<T>::load(slot_field(ring, slot, 2) + col, nuy);
+        vec4_load(reinterpret_cast<const T*>(g_smem + row), nr, a.q);
+        vec4_load(reinterpret_cast<const T*>(g_smem + row + field_bytes), nux, a.q);
+        vec4_load(reinterpret_cast<const T*>(g_smem + row + 2 * field_bytes), nuy, a.q);
         if (WALLS) {
-            const int r = it.row_first + k;
-            if (r < 0 || r >= a.ny) {  // uniform across the warp
+            const int r = row_first + k;
+            if (r < 0 || r >= a.ny) {  // uniform across the CTA
                 const float2 fac = sp(wall_factor(r, a.ny, a.xi));
                 nux[0] = mul2(nux[0], fac);
                 nux[1] = mul2(nux[1], fac);
@@ -172,15 +239,15 @@ struct RowStep {
         }
         // centre row c = r - R from its ring slot (still resident); before
         // the window is full the centre row does not exist yet
-        const int cslot = (pos - R) & kSlotMask;
         float2 cdr[2] = {sp(0.f), sp(0.f)}, cux[2] = {sp(0.f), sp(0.f)};
         float2 cuy[2] = {sp(0.f), sp(0.f)};
         if (R > 0 && (!WARM || k >= R)) {
-            if (R == 2) Vec4<T>::load(slot_field(ring, cslot, 0) + col, cdr);
-            Vec4<T>::load(slot_field(ring, cslot, 1) + col, cux);
-            Vec4<T>::load(slot_field(ring, cslot, 2) + col, cuy);
+            const uint32_t crow = lane_off + ((pos - R) & kSlotMask) * slot_bytes;
+            if (R == 2) vec4_load(reinterpret_cast<const T*>(g_smem + crow), cdr, a.q);
+            vec4_load(reinterpret_cast<const T*>(g_smem + crow + field_bytes), cux, a.q);
+            vec4_load(reinterpret_cast<const T*>(g_smem + crow + 2 * field_bytes), cuy, a.q);
             if (WALLS) {
-                const int r = it.row_first + k - R;
+                const int r = row_first + k - R;
                 if (r < 0 || r >= a.ny) {
                     const float2 fac = sp(wall_factor(r, a.ny, a.xi));
                     cux[0] = mul2(cux[0], fac);
@@ -194,118 +261,136 @@ struct RowStep {
         stream_row<R, FORCE>(nr, nux, nuy, cdr, cux, cuy, a.k, fm2, fm1, dm3, dm2, acc, odr, oux,
                              ouy);
         // destination row c - 1 = yb + k - 2R - 2 is an output row from k = 2R + 2
-        if ((!WARM || k >= warm_rows<R>()) && it.lane_stores) {
-            T* dst = static_cast<T*>(a.dst) + it.out + (size_t)(k - 2 * R - 2) * a.pitch;
-            Vec4<T>::store(dst, odr);
-            Vec4<T>::store(dst + a.plane, oux);
-            Vec4<T>::store(dst + 2 * a.plane, ouy);
+        if (!WARM || k >= warm_rows<R>()) {
+            if (stores) {
+                sat |= vec4_store(out, odr, a.q);
+                sat |= vec4_store(out + a.plane, oux, a.q);
+                sat |= vec4_store(out + 2 * a.plane, ouy, a.q);
+            }
+            out += a.pitch;
         }
     }
 };
 
-template <int R, bool FORCE, bool WALLS, typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, min_blocks<R>())
-    fd_step_stream_kernel(StreamArgs a) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int warp_bytes = kSlots * 3 * kLoadCols * (int)sizeof(T);
-    Ring<T> ring;
-    ring.slot_base = reinterpret_cast<T*>(smem + warp * warp_bytes);
-    ring.bars = reinterpret_cast<uint64_t*>(smem + kWarpsPerBlock * warp_bytes) + warp * kSlots;
-    if (lane == 0) {
-        for (int s = 0; s < kSlots; ++s) mbar_init(&ring.bars[s], 1);
+// The rows of one item for one warp; false if a copy did not land in time.
+template <int R, bool FORCE, bool WALLS, typename T, int W>
+__device__ __forceinline__ bool warp_item(const StreamArgs& a, const Item* s_item, uint32_t base,
+                                          int warp, int lane, bool& sat) {
+    const int nrows = s_item->nrows, row_first = s_item->row_first, yb = s_item->yb;
+    const uint32_t lane_off = (warp * kStrip + 4 + 4 * lane) * sizeof(T);
+    const int col = s_item->strip0 + warp * kStrip - 4 + 4 * lane;  // first column of this lane
+    const bool stores = lane >= 1 && lane <= 30 && col < a.nx;
+    T* out = static_cast<T*>(a.dst) + (size_t)yb * a.pitch + (stores ? col : 0);
+    Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
+    Acc acc = {};
+    using Step = RowStep<R, FORCE, WALLS, T, W>;
+    int k = 0;
+    for (; k + 1 < nrows; k += 2) {
+        // one vote for both rows keeps their arithmetic in one block, free
+        // to interleave
+        const bool l0 = row_landed<W, T>(base + k), l1 = row_landed<W, T>(base + k + 1);
+        if (!__all_sync(kFull, l0 && l1)) return false;
+        if (k >= warm_rows<R>()) {
+            Step::template run<false>(a, row_first, lane_off, base, k,
+                                      stores, out, sat, w0, w1, w2, w3, acc);
+            Step::template run<false>(a, row_first, lane_off, base,
+                                      k + 1, stores, out, sat, w1, w0, w3, w2, acc);
+        } else {
+            Step::template run<true>(a, row_first, lane_off, base, k,
+                                     stores, out, sat, w0, w1, w2, w3, acc);
+            Step::template run<true>(a, row_first, lane_off, base,
+                                     k + 1, stores, out, sat, w1, w0, w3, w2, acc);
+        }
+        // the centre rows of these two steps (k - R, k + 1 - R) are read for
+        // the last time: release their slots
+        __syncwarp();
+        if (lane == 0) {
+            release_row<WALLS, T, W>(a, s_item, base, k - R);
+            release_row<WALLS, T, W>(a, s_item, base, k + 1 - R);
+        }
+    }
+    if (k < nrows) {
+        if (!__all_sync(kFull, row_landed<W, T>(base + k))) return false;
+        Step::template run<true>(a, row_first, lane_off, base, k,
+                                 stores, out, sat, w0, w1, w2, w3, acc);
+    }
+    return true;
+}
+
+template <int R, bool FORCE, bool WALLS, typename T, int W>
+__global__ void __launch_bounds__(W * 32, kWarpsPerSM / W) fd_step_stream_kernel(StreamArgs a) {
+    using ring = Ring<W, T>;
+    __shared__ Item s_item;
+    // The warp index taken through a shuffle: the compiler then holds it,
+    // and the offsets derived from it, in ordinary registers (as a value it
+    // can prove warp-uniform it is kept apart, and the row loop spills).
+    const int warp = __shfl_sync(kFull, threadIdx.x >> 5, 0), lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(ring::full(s), 1);
+            *ring::count(s) = 0;
+            *ring::last(s) = -1;
+        }
         fence_mbar_init();
     }
-    __syncwarp();
-
-    uint32_t base = 0;      // ring position of the current item's row 0
-    uint32_t issued = 0;    // ring positions issued so far
-    uint32_t consumed = 0;  // ring positions waited for so far
-    bool ok = true;
-    for (int item = blockIdx.x * kWarpsPerBlock + warp; item < a.nitems && ok;
-         item += gridDim.x * kWarpsPerBlock) {
-        Item it;
-        const int strip = item % a.nstrips, seg = item / a.nstrips;
-        it.strip0 = strip * kStrip;
-        it.yb = seg * a.seg_rows;
-        it.ye = min(a.ny, it.yb + a.seg_rows);
-        it.row_first = it.yb - 1 - R;
-        it.nrows = it.ye - it.yb + 2 + 2 * R;
-        it.x0 = wrap_index(it.strip0 - 8, a.nx);
-        it.first = min(kLoadCols, a.nx - it.x0);
-        it.lane_stores = lane >= 1 && lane <= 30 && (it.strip0 - 4 + 4 * lane) < a.nx;
-        it.base = base;
-        it.out = (size_t)it.yb * a.pitch + (it.strip0 - 4 + 4 * lane);
-        // every lane is done with the slots of the previous item
-        __syncwarp();
-        // prologue: the first kSlots rows, two per issue
-        for (int k0 = 0; k0 < kSlots && k0 < it.nrows; k0 += 2)
-            issue_rows<WALLS, T>(a, ring, it, k0, min(2, it.nrows - k0), lane);
-        issued = base + min(kSlots, it.nrows);
-        Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
-        Acc acc = {};
-        int k = 0;
-        using Step = RowStep<R, FORCE, WALLS, T>;
-        for (; k + 1 < it.nrows; k += 2) {
-            // one vote for both rows keeps their arithmetic in one block,
-            // free to interleave
-            const bool l0 = row_landed(ring, it, k), l1 = row_landed(ring, it, k + 1);
-            if (!__all_sync(kFull, l0 && l1)) {
-                ok = false;
-                break;
-            }
-            if (k >= warm_rows<R>()) {
-                Step::template run<false>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
-                Step::template run<false>(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc);
-            } else {
-                Step::template run<true>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
-                Step::template run<true>(a, ring, it, lane, k + 1, w1, w0, w3, w2, acc);
-            }
-            // the centre rows of these two steps (k - R, k + 1 - R) are no
-            // longer needed: refill their slots with the rows kSlots ahead
-            __syncwarp();
-            const int m1 = k + 1 - R;
-            const int n0 = (int)(issued - base);
-            const int cnt = min(m1 + kSlots + 1, it.nrows) - n0;
-            if (m1 >= 0 && cnt > 0) {
-                issue_rows<WALLS, T>(a, ring, it, n0, cnt, lane);
-                issued += cnt;
-            }
+    uint32_t base = 0;  // ring position of the current item's row 0
+    bool failed = false, sat = false;
+    for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        // every warp is done with the previous item's slots (and the
+        // barriers are initialised); stop everywhere if a copy was lost
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
         }
-        if (ok && k < it.nrows) {
-            if (__all_sync(kFull, row_landed(ring, it, k))) {
-                Step::template run<true>(a, ring, it, lane, k, w0, w1, w2, w3, acc);
-                ++k;
-            } else {
-                ok = false;
-            }
+        if (threadIdx.x == 0) {
+            const Item it = make_item<R>(a, item, W);
+            s_item = it;
+            for (int k = 0; k < kSlots && k < it.nrows; ++k)
+                issue_row<WALLS, T, W>(a, it, base + k, k);
         }
-        consumed = base + k;
-        base += it.nrows;
+        __syncthreads();
+        const int active = s_item.active, nrows = s_item.nrows;
+        if (warp < active &&
+            !warp_item<R, FORCE, WALLS, T, W>(a, &s_item, base, warp, lane, sat))
+            failed = true;
+        base += nrows;
     }
-    if (!ok) {
+    if (std::is_same<T, int16_t>::value && __any_sync(kFull, sat) && lane == 0)
+        report_saturation(a.status);
+    if (__syncthreads_or(failed) && threadIdx.x == 0) {
         // A copy did not complete in time: record it, then give every copy
         // still in flight a bounded chance to land before the CTA exits.
-        if (lane == 0) atomicExch(a.status, FDLBM_ERR_TIMEOUT);
-        for (uint32_t n = consumed; n < issued; ++n)
-            mbar_wait_bounded(&ring.bars[n & kSlotMask], (n / kSlots) & 1u);
+        atomicExch(a.status, FDLBM_ERR_TIMEOUT);
+        for (int s = 0; s < kSlots; ++s)
+            if (*ring::last(s) >= 0)
+                mbar_wait_bounded(ring::full(s), ((uint32_t)*ring::last(s) / kSlots) & 1u);
     }
 }
 
 struct Plan {
-    int seg_rows, nsegs, nitems, blocks;
+    int W, ncstrips, seg_rows, nsegs, nitems, blocks;
 };
 
+// Warps per CTA.  Two warps share one ring: the row copies and the halo
+// columns fetched per output column halve against one-warp CTAs, and the
+// two warps' progress stays loosely coupled.  Measured on 8192^2 (FP32,
+// GLUPS, W = 2 / 3 / 4): FD-5 189.4 / 173.7 / 173.1, FD-3 221.4 / 204.9 /
+// 203.9, LW-ACM 239.0 / 216.4 / 211.0; wider CTAs lose whatever release
+// protocol they use (an acquire-release or relaxed shared-memory counter, or
+// an mbarrier arrival with its pending count: all within 1 %).
+constexpr int kWarps = 2;
+
 // Segment length that balances the waves: the critical path is
-// ceil(items / resident warps) * (segment + halo rows).
-Plan make_plan(int nx, int ny, int R, int resident_warps) {
+// ceil(items / resident CTAs) * (segment + halo rows).
+Plan make_plan(int nx, int ny, int R, int W, int resident_ctas) {
     const int nstrips = (nx + kStrip - 1) / kStrip;
-    Plan best{ny, 1, nstrips, 0};
+    Plan best{W, (nstrips + W - 1) / W, ny, 1, 0, 0};
+    best.nitems = best.ncstrips;
     long long best_cost = -1;
     for (int s = 16; s <= ny; s += (s < 128 ? 8 : 16)) {
         const int nsegs = (ny + s - 1) / s;
-        const int items = nstrips * nsegs;
-        const long long waves = (items + resident_warps - 1) / resident_warps;
+        const int items = best.ncstrips * nsegs;
+        const long long waves = (items + resident_ctas - 1) / resident_ctas;
         const long long cost = waves * (long long)(s + 2 + 2 * R);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -317,16 +402,16 @@ Plan make_plan(int nx, int ny, int R, int resident_warps) {
     if (ny < 16) {
         best.seg_rows = ny;
         best.nsegs = 1;
-        best.nitems = nstrips;
+        best.nitems = best.ncstrips;
     }
-    best.blocks = (best.nitems + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    best.blocks = best.nitems;
     return best;
 }
 
-template <int R, bool FORCE, bool WALLS, typename T>
-cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
-    auto kernel = fd_step_stream_kernel<R, FORCE, WALLS, T>;
-    const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(T) + kSlots * 8);
+template <int R, bool FORCE, bool WALLS, typename T, int W>
+cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
+    auto kernel = fd_step_stream_kernel<R, FORCE, WALLS, T, W>;
+    const size_t smem = smem_bytes(W, sizeof(T));
     if (h->stream_plan_warps == 0) {
         cudaError_t e =
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -335,10 +420,10 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
         if (e != cudaSuccess) return e;
         int sms = 0, per_sm = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerBlock * 32, smem);
-        h->stream_plan_warps = std::max(1, sms * per_sm * kWarpsPerBlock);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, W * 32, smem);
+        h->stream_plan_warps = std::max(1, sms * per_sm);  // resident CTAs
     }
-    const Plan plan = make_plan(h->p.nx, h->p.ny, R, h->stream_plan_warps);
+    const Plan plan = make_plan(h->p.nx, h->p.ny, R, W, h->stream_plan_warps);
     StreamArgs a;
     a.src = src;
     a.dst = dst;
@@ -348,6 +433,7 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     a.ny = h->p.ny;
     a.xi = (float)h->p.wall_xi;
     a.nstrips = (h->p.nx + kStrip - 1) / kStrip;
+    a.ncstrips = plan.ncstrips;
     a.seg_rows = plan.seg_rows;
     a.nsegs = plan.nsegs;
     a.nitems = plan.nitems;
@@ -364,9 +450,15 @@ cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
     const double nu = (1.0 / h->p.s_xx - 0.5) / 3.0;  // LW-ACM (Sec. 1-b)
     a.k.lw_t = (float)(2.0 * nu);
     a.k.lw_s = a.k.lw_t * 0.25f;
+    a.q = quant_of(h->p);
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
-    kernel<<<plan.blocks, kWarpsPerBlock * 32, smem, h->stream>>>(a);
+    kernel<<<plan.blocks, W * 32, smem, h->stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int R, bool FORCE, bool WALLS, typename T>
+cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
+    return launch_stream_w<R, FORCE, WALLS, T, kWarps>(h, src, dst);
 }
 
 template <bool WALLS, typename T>
@@ -398,6 +490,7 @@ cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst) {
     switch (h->p.storage) {
         case FDLBM_STORAGE_F16: return launch_stream_boundary<__half>(h, src, dst);
         case FDLBM_STORAGE_BF16: return launch_stream_boundary<__nv_bfloat16>(h, src, dst);
+        case FDLBM_STORAGE_I16: return launch_stream_boundary<int16_t>(h, src, dst);
         default: return launch_stream_boundary<float>(h, src, dst);
     }
 }

@@ -1,6 +1,6 @@
 // fd_step_tiled.cu -- general FD-LBM step kernel (Sec. 2, Eq. 2): 2-D tiles
 // staged in shared memory with a halo of r + 1 nodes.  Handles periodic and
-// channel (walls in y) lattices of any size and FP32 / FP16 / BF16 storage.
+// channel (walls in y) lattices of any size and every storage type.
 // Stencil radius r = 0 is LW-ACM (Sec. 1-b, Eq. 3): no finite differences,
 // a one-node halo for the gather.  The nine-point stencil of Sec. 2 has
 // radius 1 and also reads the diagonal neighbours, which the 2-D tile holds.
@@ -56,7 +56,7 @@ __device__ __forceinline__ float fd_deriv9(const float* p, int s, int t) {
 template <int R, bool NINE, bool WALLS, typename T>
 __global__ void __launch_bounds__(kThreads)
     fd_step_tiled_kernel(FdState<T> src, FdState<T> dst, int nx, int ny, size_t pitch,
-                         FdCoeffs c, float lw_t) {
+                         FdCoeffs c, float lw_t, int* status) {
     constexpr int H = R + 1;
     constexpr int LX = kTX + 2 * H, LY = kTY + 2 * H, LN = LX * LY;
     constexpr int GX = kTX + 2, GY = kTY + 2, GN = GX * GY;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads)
         const int x = wrap_index(x0 - H + lx, nx);
         const int y = y0 - H + ly;
         float dr, ux, uy;
-        fd_load_node<WALLS>(src, x, y, ny, pitch, c.xi, &dr, &ux, &uy);
+        fd_load_node<WALLS>(src, x, y, ny, pitch, c.xi, c.q, &dr, &ux, &uy);
         const float Jx = fmaf(dr, ux, ux), Jy = fmaf(dr, uy, uy);
         sf[0][t] = dr;
         sf[1][t] = ux;
@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
 
+    bool sat = false;
     for (int t = threadIdx.x; t < kTX * kTY; t += kThreads) {
         const int ox = t % kTX, oy = t / kTX;
         const int x = x0 + ox, y = y0 + oy;
@@ -158,10 +159,11 @@ __global__ void __launch_bounds__(kThreads)
             fd_close(p, c, &dr, &ux, &uy);
         }
         const size_t o = (size_t)y * pitch + x;
-        Storage<T>::store(dst.drho + o, dr);
-        Storage<T>::store(dst.ux + o, ux);
-        Storage<T>::store(dst.uy + o, uy);
+        sat |= Storage<T>::store(dst.drho + o, dr, c.q);
+        sat |= Storage<T>::store(dst.ux + o, ux, c.q);
+        sat |= Storage<T>::store(dst.uy + o, uy, c.q);
     }
+    if (sat) report_saturation(status);
 }
 
 template <int R, bool NINE, bool WALLS, typename T>
@@ -177,10 +179,12 @@ cudaError_t launch_typed(fdlbm_s* h, const void* src, void* dst) {
     c.fx = (float)h->p.force_x;
     c.fy = (float)h->p.force_y;
     c.xi = (float)h->p.wall_xi;
+    c.q = quant_of(h->p);
     const float lw_t = (float)(2.0 * (1.0 / h->p.s_xx - 0.5) / 3.0);  // LW-ACM: 2 nu
     dim3 grid((h->p.nx + kTX - 1) / kTX, (h->p.ny + kTY - 1) / kTY);
     fd_step_tiled_kernel<R, NINE, WALLS, T>
-        <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c, lw_t);
+        <<<grid, kThreads, 0, h->stream>>>(S, D, h->p.nx, h->p.ny, h->L.pitch, c, lw_t,
+                                           reinterpret_cast<int*>(h->ws + h->L.off_flag));
     return cudaGetLastError();
 }
 
@@ -205,6 +209,7 @@ cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst) {
     switch (h->p.storage) {
         case FDLBM_STORAGE_F16: return launch_stencil<__half>(h, src, dst);
         case FDLBM_STORAGE_BF16: return launch_stencil<__nv_bfloat16>(h, src, dst);
+        case FDLBM_STORAGE_I16: return launch_stencil<int16_t>(h, src, dst);
         default: return launch_stencil<float>(h, src, dst);
     }
 }

@@ -81,6 +81,58 @@ struct Vec4<__nv_bfloat16> {
     }
 };
 
+// Fixed-point storage (FDLBM_STORAGE_I16): 4 columns of int16 q, read as
+// q * scale and written as q = RN(v / scale) clamped to +-32767 (the
+// rounding of quantize16); store() returns true if a value saturated.
+template <>
+struct Vec4<int16_t> {
+    static __device__ __forceinline__ float2 pair(uint32_t w, float scale) {
+        const float lo = (float)((int)(w << 16) >> 16), hi = (float)((int)w >> 16);
+        return mul2(make_float2(lo, hi), sp(scale));
+    }
+    static __device__ __forceinline__ void load(const int16_t* p, float2 v[2], Quant q) {
+        const uint2 w = *reinterpret_cast<const uint2*>(p);
+        v[0] = pair(w.x, q.scale);
+        v[1] = pair(w.y, q.scale);
+    }
+    static __device__ __forceinline__ uint32_t pack(float2 v, float inv, bool& sat) {
+        const float2 t = mul2(v, sp(inv));
+        sat |= !(fabsf(t.x) <= 32767.f) || !(fabsf(t.y) <= 32767.f);
+        const float cx = fminf(fmaxf(t.x, -32767.f), 32767.f);
+        const float cy = fminf(fmaxf(t.y, -32767.f), 32767.f);
+        const float2 m = add2(make_float2(cx, cy), sp(12582912.f));  // 1.5 * 2^23
+        return (__float_as_uint(m.x) & 0xffffu) | (__float_as_uint(m.y) << 16);
+    }
+    static __device__ __forceinline__ bool store(int16_t* p, const float2 v[2], Quant q) {
+        bool sat = false;
+        uint2 w;
+        w.x = pack(v[0], q.inv, sat);
+        w.y = pack(v[1], q.inv, sat);
+        *reinterpret_cast<uint2*>(p) = w;
+        return sat;
+    }
+};
+
+// The floating-point storage types through the same interface (no scale,
+// never saturated).
+template <typename T>
+__device__ __forceinline__ void vec4_load(const T* p, float2 v[2], Quant) {
+    Vec4<T>::load(p, v);
+}
+template <>
+__device__ __forceinline__ void vec4_load<int16_t>(const int16_t* p, float2 v[2], Quant q) {
+    Vec4<int16_t>::load(p, v, q);
+}
+template <typename T>
+__device__ __forceinline__ bool vec4_store(T* p, const float2 v[2], Quant) {
+    Vec4<T>::store(p, v);
+    return false;
+}
+template <>
+__device__ __forceinline__ bool vec4_store<int16_t>(int16_t* p, const float2 v[2], Quant q) {
+    return Vec4<int16_t>::store(p, v, q);
+}
+
 // Fields of the y window: rho - 1, Jx, Jy, Jx Jy / rho, Jy Jy / rho, each as
 // two column pairs: v[f][0] = columns (0, 1), v[f][1] = columns (2, 3).
 enum { W_R = 0, W_JX, W_JY, W_PXY, W_PYY, W_N };

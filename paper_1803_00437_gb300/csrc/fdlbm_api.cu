@@ -65,8 +65,11 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->boundary != FDLBM_BOUNDARY_PERIODIC && p->boundary != FDLBM_BOUNDARY_WALLS_Y)
         return fail(FDLBM_ERR_INVALID, "boundary must be PERIODIC or WALLS_Y");
     if (p->storage != FDLBM_STORAGE_F32 && p->storage != FDLBM_STORAGE_F16 &&
-        p->storage != FDLBM_STORAGE_BF16)
-        return fail(FDLBM_ERR_INVALID, "storage must be F32, F16 or BF16");
+        p->storage != FDLBM_STORAGE_BF16 && p->storage != FDLBM_STORAGE_I16)
+        return fail(FDLBM_ERR_INVALID, "storage must be F32, F16, BF16 or I16");
+    if (p->storage == FDLBM_STORAGE_I16 &&
+        !(p->storage_range > 0.0 && p->storage_range < 1e30))
+        return fail(FDLBM_ERR_INVALID, "I16 storage needs a finite storage_range > 0");
     if ((p->flags & ~(FDLBM_FLAG_TILED | FDLBM_FLAG_STREAM)) != 0)
         return fail(FDLBM_ERR_INVALID, "unknown flags");
     if ((p->flags & FDLBM_FLAG_TILED) && (p->flags & FDLBM_FLAG_STREAM))
@@ -94,6 +97,15 @@ static int check_params(const fdlbm_params* p, char* why, size_t n) {
     if (p->scheme == FDLBM_SCHEME_FD9 && (p->flags & FDLBM_FLAG_STREAM))
         return fail(FDLBM_ERR_UNSUPPORTED, "FD9 runs on the tiled kernel only");
     return FDLBM_OK;
+}
+
+Quant quant_of(const fdlbm_params& p) {
+    Quant q;
+    if (p.storage == FDLBM_STORAGE_I16) {
+        q.scale = (float)(p.storage_range / 32767.0);
+        q.inv = 1.f / q.scale;
+    }
+    return q;
 }
 
 bool compute_layout(const fdlbm_params& p, Layout* L) {
@@ -155,6 +167,15 @@ struct DeviceGuard {
     }
 };
 
+static const char* device_error_text(int flag) {
+    switch (flag) {
+        case FDLBM_ERR_TIMEOUT: return "FDLBM_ERR_TIMEOUT (a bounded wait expired)";
+        case FDLBM_ERR_RANGE:
+            return "FDLBM_ERR_RANGE (a value outside storage_range was stored saturated)";
+        default: return "an error";
+    }
+}
+
 // Read (and clear) the device status word after the stream has drained.
 static int device_status(fdlbm_t* h) {
     int flag = 0;
@@ -164,8 +185,7 @@ static int device_status(fdlbm_t* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "status read");
     if (flag != 0) {
         cudaMemsetAsync(dflag, 0, sizeof(int), h->stream);
-        return set_error(h, flag, "device reported %s (a bounded wait expired)",
-                         flag == FDLBM_ERR_TIMEOUT ? "FDLBM_ERR_TIMEOUT" : "an error");
+        return set_error(h, flag, "device reported %s", device_error_text(flag));
     }
     return FDLBM_OK;
 }
@@ -419,8 +439,7 @@ int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out) {
     const int flag = h->host_io->flag;
     if (flag != 0) {
         cudaMemsetAsync(dflag, 0, sizeof(int), h->stream);
-        return set_error(h, flag, "device reported %s (a bounded wait expired)",
-                         flag == FDLBM_ERR_TIMEOUT ? "FDLBM_ERR_TIMEOUT" : "an error");
+        return set_error(h, flag, "device reported %s", device_error_text(flag));
     }
     return FDLBM_OK;
 }
@@ -457,6 +476,7 @@ const char* fdlbm_status_string(int s) {
         case FDLBM_ERR_CUDA: return "FDLBM_ERR_CUDA";
         case FDLBM_ERR_DIVERGED: return "FDLBM_ERR_DIVERGED";
         case FDLBM_ERR_TIMEOUT: return "FDLBM_ERR_TIMEOUT";
+        case FDLBM_ERR_RANGE: return "FDLBM_ERR_RANGE";
         default: return "FDLBM_UNKNOWN_STATUS";
     }
 }

@@ -17,6 +17,18 @@
 namespace fdlbm {
 
 // ---- storage types --------------------------------------------------------
+//
+// Every type is read into FP32 and written from FP32 (round to nearest).
+// FDLBM_STORAGE_I16 is fixed point: a stored q stands for q * scale with
+// scale = storage_range / 32767, written as q = RN(v * (1 / scale)) clamped
+// to +-32767; a value outside the range (or not finite) saturates and the
+// store reports it.  The floating-point types ignore the scale and never
+// saturate.
+
+struct Quant {
+    float scale = 1.f;  // value of one fixed-point step
+    float inv = 1.f;    // 1 / scale, rounded to FP32
+};
 
 template <typename T>
 struct Storage;
@@ -25,12 +37,22 @@ template <>
 struct Storage<float> {
     static __device__ __forceinline__ float load(const float* p) { return *p; }
     static __device__ __forceinline__ void store(float* p, float v) { *p = v; }
+    static __device__ __forceinline__ float load(const float* p, Quant) { return *p; }
+    static __device__ __forceinline__ bool store(float* p, float v, Quant) {
+        *p = v;
+        return false;
+    }
 };
 
 template <>
 struct Storage<__half> {
     static __device__ __forceinline__ float load(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void store(__half* p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ float load(const __half* p, Quant) { return load(p); }
+    static __device__ __forceinline__ bool store(__half* p, float v, Quant) {
+        store(p, v);
+        return false;
+    }
 };
 
 template <>
@@ -40,6 +62,34 @@ struct Storage<__nv_bfloat16> {
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float v) {
         *p = __float2bfloat16_rn(v);
+    }
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, Quant) { return load(p); }
+    static __device__ __forceinline__ bool store(__nv_bfloat16* p, float v, Quant) {
+        store(p, v);
+        return false;
+    }
+};
+
+// Fixed-point step of a value: t = v / scale, rounded to the nearest integer
+// (ties to even) by adding 1.5 * 2^23, which leaves the integer in the low
+// mantissa bits; |t| is clamped to 32767 first.  Returns q; *sat is set when
+// |t| > 32767 or t is not finite.
+__device__ __forceinline__ int quantize16(float v, Quant q, bool* sat) {
+    const float t = v * q.inv;
+    *sat = !(fabsf(t) <= 32767.f);
+    const float c = fminf(fmaxf(t, -32767.f), 32767.f);  // a NaN becomes -32767
+    return __float_as_int(c + 12582912.f) - 0x4B400000;
+}
+
+template <>
+struct Storage<int16_t> {
+    static __device__ __forceinline__ float load(const int16_t* p, Quant q) {
+        return (float)*p * q.scale;
+    }
+    static __device__ __forceinline__ bool store(int16_t* p, float v, Quant q) {
+        bool sat;
+        *p = (int16_t)quantize16(v, q, &sat);
+        return sat;
     }
 };
 
@@ -63,6 +113,7 @@ struct FdCoeffs {
     float a_xx;   // 1 - 1/s_xx (factor of theta_XX, theta_XY)
     float fx, fy; // body force
     float xi;     // wall offset
+    Quant q;      // fixed-point scale (FDLBM_STORAGE_I16)
 };
 
 struct MrtCoeffs {
@@ -90,6 +141,15 @@ constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs (full occupancy at 256 threa
 constexpr int kReduceSlots = 4;     // doubles per block partial
 
 bool compute_layout(const fdlbm_params& p, Layout* L);
+
+// Fixed-point scale of a lattice's storage (scale 1 unless FDLBM_STORAGE_I16).
+Quant quant_of(const fdlbm_params& p);
+
+// Record a saturated fixed-point store in the device status word (no other
+// error is overwritten).
+__device__ __forceinline__ void report_saturation(int* status) {
+    atomicCAS(status, 0, FDLBM_ERR_RANGE);
+}
 
 }  // namespace fdlbm
 

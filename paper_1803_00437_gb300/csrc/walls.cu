@@ -102,6 +102,8 @@ int fdlbm_set_walls(fdlbm_t* h, const uint8_t* kind, int64_t nvirt, const int64_
         return walls_error(h, FDLBM_ERR_UNSUPPORTED, "set_walls: FD-LBM (FD3, FD5, FD9) only");
     if (p.boundary != FDLBM_BOUNDARY_PERIODIC)
         return walls_error(h, FDLBM_ERR_UNSUPPORTED, "set_walls: needs a periodic lattice");
+    if (h->p.storage == FDLBM_STORAGE_I16)
+        return walls_error(h, FDLBM_ERR_UNSUPPORTED, "set_walls: not with I16 storage");
     if (h->L.plane >= ((size_t)1 << 31))
         return walls_error(h, FDLBM_ERR_UNSUPPORTED, "set_walls: plane above 2^31 elements");
     const int nx = p.nx, ny = p.ny;

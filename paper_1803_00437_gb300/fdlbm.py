@@ -18,11 +18,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfdlbm.so")
 
 # include/fdlbm.h constants
-OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT = (
-    0, -1, -2, -3, -4, -5, -6)
+OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_RANGE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
 SCHEMES = {"fd3": 3, "fd5": 5, "fd9": 9, "mrt": 100, "lwacm": 200}
 BOUNDARIES = {"periodic": 0, "walls_y": 1}
-STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "i16": 3}
 REDUCE = {"mass": 0, "momentum": 1, "energy": 2, "mode": 3, "maxabs": 4}
 FLAG_TILED = 1
 FLAG_STREAM = 2
@@ -44,6 +44,7 @@ class Params(ctypes.Structure):
         ("s_q", ctypes.c_double), ("s_eps", ctypes.c_double),
         ("wall_xi", ctypes.c_double),
         ("force_x", ctypes.c_double), ("force_y", ctypes.c_double),
+        ("storage_range", ctypes.c_double),
     ]
 
 
@@ -166,13 +167,16 @@ class LatticeConfig:
     wall_xi: float = 0.5
     force: tuple = (0.0, 0.0)
     flags: int = 0
+    storage_range: float = 0.0  # "i16" storage: largest |value| representable
+
 
     def params(self) -> Params:
         s_q = self.s_q if self.s_q is not None else S_Q_QUARTIC
         return Params(int(self.nx), int(self.ny), SCHEMES[self.scheme],
                       BOUNDARIES[self.boundary], STORAGES[self.storage], int(self.flags),
                       float(self.s_xx), float(self.s_e), float(s_q), float(self.s_eps),
-                      float(self.wall_xi), float(self.force[0]), float(self.force[1]))
+                      float(self.wall_xi), float(self.force[0]), float(self.force[1]),
+                      float(self.storage_range))
 
 
 def workspace_size(cfg: LatticeConfig) -> int:

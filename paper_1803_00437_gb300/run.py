@@ -20,6 +20,7 @@ def main(argv=None):
     ap.add_argument("--scheme", default="fd5", choices=["fd3", "fd5", "fd9", "mrt", "lwacm"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=0, help="untimed steps before the timed ones")
     ap.add_argument("--nu", type=float, default=0.01)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--reduce", nargs="*", default=[],
@@ -34,6 +35,7 @@ def main(argv=None):
     lat = F.Lattice(F.LatticeConfig(n, n, args.scheme, s_xx=F.nu_to_s(args.nu), s_e=1.5,
                                     storage=args.storage))
     lat.init_modes(inputs.random_modes(n, n, args.modes, 1e-3, seed=inputs.seed_for(1)))
+    lat.step(args.warmup)
     lat.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lat.stream)

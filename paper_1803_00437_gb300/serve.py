@@ -96,8 +96,11 @@ class Server:
 
     def __init__(self, hbm_budget: int = 80 << 30, max_slots: int = 1024, max_side: int = 4096,
                  scheme: str = "fd5", run_steps: int = 64, segment_rows: int | None = None,
-                 device=None):
+                 device=None, return_fields: bool = False):
         self.scheme = scheme
+        # also hand each finished request its final (rho - 1, ux, uy) fields
+        # (host float32 arrays [ny, nx]), copied before its slot is released
+        self.return_fields = bool(return_fields)
         self.run_steps = int(run_steps)
         self.batch = F.Batch(scheme, max_lattices=max_slots, arena_bytes=int(hbm_budget),
                              max_side=max_side, device=device)
@@ -139,6 +142,10 @@ class Server:
         if req.modes:
             md = req.modes[0]
             res["mode0"] = [float(v) for v in b.reduce(slot, "mode", (md.m, md.n))]
+        if self.return_fields:
+            fields = b.moments(slot)
+            res["fields"] = [t.cpu().numpy() for t in fields]
+            b.sync()
         req.result = res
         req.finished = now
         b.remove(slot)

@@ -141,3 +141,18 @@ def test_mrt_s_q_sentinel(lib):
     assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", s_q=1.2)) > 0
     for bad in (-0.5, 2.0, 2.5):
         assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", s_q=bad)) == 0, bad
+
+
+def test_fixed_point_storage_parameters(lib):
+    """FDLBM_STORAGE_I16 needs a finite storage_range > 0, is FD-LBM only,
+    and stores 2 bytes per field like FP16."""
+    from paper_1803_00437_gb300 import fdlbm as F
+    f16 = F.workspace_size(F.LatticeConfig(512, 48, "fd5", storage="f16"))
+    assert F.workspace_size(F.LatticeConfig(512, 48, "fd5", storage="i16",
+                                            storage_range=0.02)) == f16
+    for bad in (0.0, -1.0, float("inf"), float("nan")):
+        assert F.workspace_size(F.LatticeConfig(512, 48, "fd5", storage="i16",
+                                                storage_range=bad)) == 0, bad
+    assert F.workspace_size(F.LatticeConfig(64, 48, "mrt", storage="i16",
+                                            storage_range=0.02)) == 0
+    assert F.status_string(F.ERR_RANGE) == "FDLBM_ERR_RANGE"

@@ -34,12 +34,15 @@ def _run(cfg, fields, n, walls=None):
     ("fd5", "bf16", 1, (96, 40)),
     ("lwacm", "f32", 2, (256, 48)),
     ("fd9", "f32", 0, (64, 48)),
+    ("fd5", "i16", 2, (256, 64)),
+    ("fd3", "i16", 1, (100, 37)),
 ])
 def test_resume_from_moments_is_exact(scheme, storage, flags, shape):
     from paper_1803_00437_gb300 import fdlbm as F
     nx, ny = shape
     cfg = F.LatticeConfig(nx, ny, scheme, s_xx=F.nu_to_s(0.15 if scheme == "fd9" else 0.02),
-                          s_e=1.5, storage=storage, flags=flags)
+                          s_e=1.5, storage=storage, flags=flags,
+                          storage_range=0.05 if storage == "i16" else 0.0)
     f = as_f32(inputs.random_fields(nx, ny, 0.02, seed=nx + ny, rho_amp=0.01))
     straight = _run(cfg, f, 70)
     checkpoint = _run(cfg, f, 30)

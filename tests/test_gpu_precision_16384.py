@@ -21,6 +21,10 @@ initial field amplitude:
   BF16 (u_s = 2^-8): the per-step change is below the storage resolution,
         so the decay is rounded away; checked to stay finite and bounded
         only (recorded, not a target).
+  I16 (fixed point, range 1.25 of the initial field amplitude, spacing
+        3.8e-5 of it): sqrt(n) half-spacings ~ 1.4e-3; asserted at the
+        reduced-storage target B = 2e-3.
+FP16 and BF16 do not meet the 2e-3 target; I16 does.
 Decay rates follow from the field bound: a mode projection is an average
 of (-ky ux + kx uy)/k against a unit phase, so its error is at most sqrt(2) B
 (absolute); for a mode whose oracle amplitude after n steps is a_n >= 10 B,
@@ -42,7 +46,8 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 TILE, REP, STEPS, AMP, NU = 512, 32, 5000, 1e-3, 0.01
 N = TILE * REP
 # field error bound B / initial field amplitude
-BOUNDS = {"f32": 1e-5, "f16": 5e-2, "bf16": 1.0}
+BOUNDS = {"f32": 1e-5, "f16": 5e-2, "bf16": 1.0, "i16": 2e-3}
+RANGE_OVER_FIELD = 1.25  # I16 storage range, relative to the initial max |u|
 
 
 def _fold(t):
@@ -74,13 +79,15 @@ def tile_reference(oracle):
     return modes, f, ref
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "i16"])
 def test_16384_slices_and_decay_vs_oracle(tile_reference, storage):
     import torch
     from oracle import linear
     from paper_1803_00437_gb300 import fdlbm as F
     modes, f, ref = tile_reference
-    cfg = F.LatticeConfig(N, N, "fd5", s_xx=F.nu_to_s(NU), s_e=1.5, storage=storage)
+    field0 = max(float(np.abs(f[1]).max()), float(np.abs(f[2]).max()))
+    cfg = F.LatticeConfig(N, N, "fd5", s_xx=F.nu_to_s(NU), s_e=1.5, storage=storage,
+                          storage_range=RANGE_OVER_FIELD * field0 if storage == "i16" else 0.0)
     lat = F.Lattice(cfg)
     dev = [torch.from_numpy(a).cuda().repeat(REP, REP) for a in f]
     lat.init(*dev)

@@ -1,6 +1,8 @@
-"""Serving with continuous batching: every request's result is the same when
-it is served alone and when it shares the GPU with a mix of others that
-arrive while it runs; admission waits for HBM budget."""
+"""Serving with continuous batching: every request of a mixed stream is
+checked against the FP64 oracle element by element (its own kind, mode list,
+nu, force and step count from the same FP32 start); its final fields are the
+same, bit for bit, when it is served alone and when it shares the GPU with a
+mix of others that arrive while it runs; admission waits for HBM budget."""
 import numpy as np
 import pytest
 
@@ -29,20 +31,65 @@ def _same(a, b):
     return True
 
 
-def test_results_alone_equal_results_in_the_mix():
+def _initial_fields(req):
+    """The request's start as the device evaluates it: its transverse modes
+    (rest for a channel), rounded to FP32 once."""
+    from paper_1803_00437_gb300 import inputs
+    from parity_util import as_f32
+    if req.modes:
+        return as_f32(inputs.transverse_modes(req.nx, req.ny, req.modes))
+    z = np.zeros((req.ny, req.nx))
+    return as_f32((z, z, z))
+
+
+@pytest.fixture(scope="module")
+def served_mix():
     from paper_1803_00437_gb300 import serve
-    mix = serve.Server(hbm_budget=256 << 20, max_slots=16, max_side=512, run_steps=32)
+    mix = serve.Server(hbm_budget=256 << 20, max_slots=16, max_side=512, run_steps=32,
+                       return_fields=True)
     done = mix.serve(_stream())
+    return done
+
+
+def test_every_served_request_matches_the_oracle(served_mix, oracle):
+    """Each request's final fields against the oracle run of its own
+    configuration.  Tolerance (FP32): 1e-5 of the initial wave amplitude for
+    waves; channels start at rest, so their scale is the oracle's final
+    max |u|, with the FP32 forced-flow bound max(1e-5, 6e-8 n) (each step adds
+    F to u with a relative rounding of ~6e-8 of u)."""
+    from paper_1803_00437_gb300 import serve
+    from parity_util import amplitude, max_err, oracle_run
+    done = served_mix
     assert len(done) == 14 and {r.kind for r in done} == set(serve.KINDS)
+    for r in done:
+        f = _initial_fields(r)
+        ref = oracle_run(oracle, r.config("fd5"), f, r.steps)
+        got = [a.astype(np.float64) for a in r.result["fields"]]
+        if r.kind == "poiseuille":
+            scale = max(float(np.abs(ref[1]).max()), 1e-30)
+            tol = max(1e-5, 6e-8 * r.steps)
+        else:
+            scale, tol = amplitude(f), 1e-5
+        err = max_err(got, ref, scale)
+        assert err <= tol, (r.rid, r.kind, r.nx, r.ny, r.steps, err)
+
+
+def test_results_alone_equal_results_in_the_mix(served_mix):
+    from paper_1803_00437_gb300 import serve
+    done = served_mix
     # several requests overlapped on the device
     spans = sorted((r.admitted, r.finished) for r in done)
     assert any(a2 < f1 for (a1, f1), (a2, f2) in zip(spans, spans[1:]))
     for r in done:
-        alone = serve.Server(hbm_budget=64 << 20, max_slots=1, max_side=512, run_steps=32)
+        alone = serve.Server(hbm_budget=64 << 20, max_slots=1, max_side=512, run_steps=32,
+                             return_fields=True)
         solo = _stream()[r.rid]
         solo.arrival = 0.0
         (res,) = alone.serve([solo])
-        assert _same(r.result, res.result), (r.rid, r.kind, r.result, res.result)
+        for a, b in zip(r.result["fields"], res.result["fields"]):
+            assert np.array_equal(a, b), (r.rid, r.kind)
+        scalars = {k: v for k, v in r.result.items() if k != "fields"}
+        assert _same(scalars, res.result), (r.rid, r.kind, scalars, res.result)
 
 
 def test_admission_waits_for_budget():
