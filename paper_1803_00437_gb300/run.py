@@ -18,7 +18,9 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--scheme", default="fd5", choices=["fd3", "fd5", "fd9", "mrt", "lwacm"])
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "i16"])
+    ap.add_argument("--range", type=float, default=0.02,
+                    help="largest |value| of the i16 fixed-point storage")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=0, help="untimed steps before the timed ones")
     ap.add_argument("--nu", type=float, default=0.01)
@@ -33,7 +35,7 @@ def main(argv=None):
     build.build()
     n = args.side
     lat = F.Lattice(F.LatticeConfig(n, n, args.scheme, s_xx=F.nu_to_s(args.nu), s_e=1.5,
-                                    storage=args.storage))
+                                    storage=args.storage, storage_range=args.range))
     lat.init_modes(inputs.random_modes(n, n, args.modes, 1e-3, seed=inputs.seed_for(1)))
     lat.step(args.warmup)
     lat.sync()
