@@ -72,12 +72,6 @@ struct StreamArgs {
     StreamCoeffs k;
     Quant q;          // fixed-point scale (FDLBM_STORAGE_I16)
     int* status;      // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
-    // Several steps per launch (nsteps > 1; one item per CTA, all CTAs
-    // resident): step s reads src (s even) or dst (s odd) and writes the
-    // other; items[i] records epoch + s + 1 once item i has finished step s.
-    int nsteps;
-    int* items;
-    uint32_t epoch;
 };
 
 // Per-item constants, uniform over the CTA.
@@ -142,15 +136,12 @@ struct Ring {
 
 // Copy ring row k of the item (ring position pos) into its slot; one thread.
 template <bool WALLS, typename T, int W>
-__device__ __forceinline__ void issue_row(const StreamArgs& a, const T* src, const Item& it,
-                                          uint32_t pos, int k) {
+__device__ __forceinline__ void issue_row(const StreamArgs& a, const Item& it, uint32_t pos,
+                                          int k) {
     using ring = Ring<W, T>;
     const int slot = pos & kSlotMask;
     uint64_t* bar = ring::full(slot);
-    // orders this CTA's earlier generic reads of the slot, and the rows other
-    // CTAs wrote in global memory in an earlier step of the launch (seen
-    // through an acquire), before the copy's async-proxy accesses
-    fence_proxy_async();
+    fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, 3u * ring::cols * sizeof(T));
     int r = it.row_first + k;
     int rref = r;
@@ -163,6 +154,7 @@ __device__ __forceinline__ void issue_row(const StreamArgs& a, const T* src, con
         r = wall_edge(r, a.ny);
     }
     T* dst = reinterpret_cast<T*>(g_smem) + (size_t)slot * 3 * ring::cols;
+    const T* src = static_cast<const T*>(a.src);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const T* rowp = src + f * a.plane + (size_t)(f == 0 ? r : rref) * a.pitch;
@@ -204,14 +196,14 @@ __device__ __forceinline__ uint32_t release_inc(uint32_t* counter, uint32_t last
 // the item's description is read from shared memory (it is needed only
 // here, so it is not held in registers through the row loop).
 template <bool WALLS, typename T, int W>
-__device__ __forceinline__ void release_row(const StreamArgs& a, const T* src, const Item* s_item,
+__device__ __forceinline__ void release_row(const StreamArgs& a, const Item* s_item,
                                             uint32_t base, int m) {
     const int nrows = s_item->nrows, active = s_item->active;
     if (m < 0 || m + kSlots >= nrows) return;  // no refill follows this row
     const uint32_t pos = base + m;
     if (release_inc(Ring<W, T>::count(pos & kSlotMask), active - 1) == (uint32_t)(active - 1)) {
         const Item it = *s_item;
-        issue_row<WALLS, T, W>(a, src, it, pos + kSlots, m + kSlots);
+        issue_row<WALLS, T, W>(a, it, pos + kSlots, m + kSlots);
     }
 }
 
@@ -282,14 +274,13 @@ struct RowStep {
 
 // The rows of one item for one warp; false if a copy did not land in time.
 template <int R, bool FORCE, bool WALLS, typename T, int W>
-__device__ __forceinline__ bool warp_item(const StreamArgs& a, const T* src, T* dst,
-                                          const Item* s_item, uint32_t base, int warp, int lane,
-                                          bool& sat) {
+__device__ __forceinline__ bool warp_item(const StreamArgs& a, const Item* s_item, uint32_t base,
+                                          int warp, int lane, bool& sat) {
     const int nrows = s_item->nrows, row_first = s_item->row_first, yb = s_item->yb;
     const uint32_t lane_off = (warp * kStrip + 4 + 4 * lane) * sizeof(T);
     const int col = s_item->strip0 + warp * kStrip - 4 + 4 * lane;  // first column of this lane
     const bool stores = lane >= 1 && lane <= 30 && col < a.nx;
-    T* out = dst + (size_t)yb * a.pitch + (stores ? col : 0);
+    T* out = static_cast<T*>(a.dst) + (size_t)yb * a.pitch + (stores ? col : 0);
     Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
     Acc acc = {};
     using Step = RowStep<R, FORCE, WALLS, T, W>;
@@ -314,8 +305,8 @@ __device__ __forceinline__ bool warp_item(const StreamArgs& a, const T* src, T* 
         // the last time: release their slots
         __syncwarp();
         if (lane == 0) {
-            release_row<WALLS, T, W>(a, src, s_item, base, k - R);
-            release_row<WALLS, T, W>(a, src, s_item, base, k + 1 - R);
+            release_row<WALLS, T, W>(a, s_item, base, k - R);
+            release_row<WALLS, T, W>(a, s_item, base, k + 1 - R);
         }
     }
     if (k < nrows) {
@@ -326,50 +317,10 @@ __device__ __forceinline__ bool warp_item(const StreamArgs& a, const T* src, T* 
     return true;
 }
 
-// Records of the items a multi-step launch waits for: the 3 x 3 items
-// around `item` (strips wrap in x; row segments wrap in y unless the lattice
-// is a channel), each the state of its rows and columns after a step.
-constexpr uint32_t kRecordSpinLimit = 1u << 24;
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Thread 0 of a CTA: wait (bounded) until the neighbours of `item` have
-// recorded `target`, i.e. finished the previous step, so that the rows this
-// item reads are written and the rows it writes are no longer read.
-template <bool WALLS>
-__device__ __forceinline__ bool wait_neighbours(const StreamArgs& a, int item, uint32_t target) {
-    const int cs = item % a.ncstrips, seg = item / a.ncstrips;
-    for (int dy = -1; dy <= 1; ++dy) {
-        int sg = seg + dy;
-        if (sg < 0 || sg >= a.nsegs) {
-            if (WALLS) continue;
-            sg = (sg + a.nsegs) % a.nsegs;
-        }
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int* rec = a.items + sg * a.ncstrips + (cs + dx + a.ncstrips) % a.ncstrips;
-            uint32_t polls = 0;
-            while ((int)((uint32_t)ld_acquire(rec) - target) < 0) {
-                if (++polls > kRecordSpinLimit) return false;
-                __nanosleep(64);
-            }
-        }
-    }
-    return true;
-}
-
 template <int R, bool FORCE, bool WALLS, typename T, int W>
 __global__ void __launch_bounds__(W * 32, kWarpsPerSM / W) fd_step_stream_kernel(StreamArgs a) {
     using ring = Ring<W, T>;
     __shared__ Item s_item;
-    __shared__ int s_stop;
     // The warp index taken through a shuffle: the compiler then holds it,
     // and the offsets derived from it, in ordinary registers (as a value it
     // can prove warp-uniform it is kept apart, and the row loop spills).
@@ -384,53 +335,31 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSM / W) fd_step_stream_kernel
     }
     uint32_t base = 0;  // ring position of the current item's row 0
     bool failed = false, sat = false;
-    for (int step = 0; step < a.nsteps && !failed; ++step) {
-        const T* src = static_cast<const T*>((step & 1) ? a.dst : a.src);
-        T* dst = static_cast<T*>(const_cast<void*>((step & 1) ? a.src : a.dst));
-        for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-            // every warp is done with the previous item's slots (and the
-            // barriers are initialised); stop everywhere if a copy was lost
-            if (__syncthreads_or(failed)) {
-                failed = true;
-                break;
-            }
-            if (threadIdx.x == 0) {
-                const Item it = make_item<R>(a, item, W);
-                s_item = it;
-                s_stop = step > 0 && !wait_neighbours<WALLS>(a, item, a.epoch + step);
-                if (!s_stop)
-                    for (int k = 0; k < kSlots && k < it.nrows; ++k)
-                        issue_row<WALLS, T, W>(a, src, it, base + k, k);
-            }
-            __syncthreads();
-            if (s_stop) {  // a neighbour never finished its step: give up
-                failed = true;
-                break;
-            }
-            const int active = s_item.active, nrows = s_item.nrows;
-            if (warp < active &&
-                !warp_item<R, FORCE, WALLS, T, W>(a, src, dst, &s_item, base, warp, lane, sat))
-                failed = true;
-            base += nrows;
+    for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+        // every warp is done with the previous item's slots (and the
+        // barriers are initialised); stop everywhere if a copy was lost
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
         }
-        if (a.nsteps > 1) {
-            // the item's rows are written: make them visible, then record it
-            __threadfence();
-            if (__syncthreads_or(failed)) {
-                failed = true;
-                break;
-            }
-            if (threadIdx.x == 0)
-                for (int item = blockIdx.x; item < a.nitems; item += gridDim.x)
-                    st_release(a.items + item, (int)(a.epoch + step + 1));
+        if (threadIdx.x == 0) {
+            const Item it = make_item<R>(a, item, W);
+            s_item = it;
+            for (int k = 0; k < kSlots && k < it.nrows; ++k)
+                issue_row<WALLS, T, W>(a, it, base + k, k);
         }
+        __syncthreads();
+        const int active = s_item.active, nrows = s_item.nrows;
+        if (warp < active &&
+            !warp_item<R, FORCE, WALLS, T, W>(a, &s_item, base, warp, lane, sat))
+            failed = true;
+        base += nrows;
     }
     if (std::is_same<T, int16_t>::value && __any_sync(kFull, sat) && lane == 0)
         report_saturation(a.status);
     if (__syncthreads_or(failed) && threadIdx.x == 0) {
-        // A copy or a neighbour did not complete in time: record it, then
-        // give every copy still in flight a bounded chance to land before
-        // the CTA exits.
+        // A copy did not complete in time: record it, then give every copy
+        // still in flight a bounded chance to land before the CTA exits.
         atomicExch(a.status, FDLBM_ERR_TIMEOUT);
         for (int s = 0; s < kSlots; ++s)
             if (*ring::last(s) >= 0)
@@ -483,14 +412,8 @@ Plan make_plan(int nx, int ny, int R, int W, int resident_ctas) {
     return best;
 }
 
-constexpr int kMaxStepsPerLaunch = 64;
-
-// One launch: a single step (nsteps_wanted == 1, *done = 1), or several steps
-// in one cooperative launch when every item has its own resident CTA
-// (*done = steps launched; 0 if the lattice does not allow it).
 template <int R, bool FORCE, bool WALLS, typename T, int W>
-cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst, int64_t nsteps_wanted,
-                            int* done) {
+cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
     auto kernel = fd_step_stream_kernel<R, FORCE, WALLS, T, W>;
     const size_t smem = smem_bytes(W, sizeof(T));
     if (h->stream_plan_warps == 0) {
@@ -533,55 +456,31 @@ cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst, int64_t nste
     a.k.lw_s = a.k.lw_t * 0.25f;
     a.q = quant_of(h->p);
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
-    a.nsteps = 1;
-    a.items = nullptr;
-    a.epoch = 0;
-    if (nsteps_wanted <= 1) {
-        *done = 1;
-        kernel<<<plan.blocks, W * 32, smem, h->stream>>>(a);
-        return cudaGetLastError();
-    }
-    *done = 0;
-    if (plan.nitems > h->stream_plan_warps ||
-        (size_t)plan.nitems * sizeof(int) > h->L.items_bytes)
-        return cudaSuccess;  // more items than resident CTAs: one launch per step
-    a.nsteps = (int)std::min<int64_t>(nsteps_wanted, kMaxStepsPerLaunch);
-    a.items = reinterpret_cast<int*>(h->ws + h->L.off_items);
-    a.epoch = h->item_epoch;
-    void* params[] = {&a};
-    cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kernel),
-                                                dim3(plan.blocks), dim3(W * 32), params, smem,
-                                                h->stream);
-    if (e != cudaSuccess) return e;
-    h->item_epoch += (uint32_t)a.nsteps;
-    *done = a.nsteps;
-    return cudaSuccess;
+    kernel<<<plan.blocks, W * 32, smem, h->stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <int R, bool FORCE, bool WALLS, typename T>
-cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst, int64_t n, int* done) {
-    return launch_stream_w<R, FORCE, WALLS, T, kWarps>(h, src, dst, n, done);
+cudaError_t launch_stream_typed(fdlbm_s* h, const void* src, void* dst) {
+    return launch_stream_w<R, FORCE, WALLS, T, kWarps>(h, src, dst);
 }
 
 template <bool WALLS, typename T>
-cudaError_t launch_stream_stencil(fdlbm_s* h, const void* src, void* dst, int64_t n, int* done) {
+cudaError_t launch_stream_stencil(fdlbm_s* h, const void* src, void* dst) {
     const bool force = h->p.force_x != 0.0 || h->p.force_y != 0.0;
     // LW-ACM: no finite differences (radius 0), periodic, no force
-    if (h->p.scheme == FDLBM_SCHEME_LWACM)
-        return launch_stream_typed<0, false, false, T>(h, src, dst, n, done);
+    if (h->p.scheme == FDLBM_SCHEME_LWACM) return launch_stream_typed<0, false, false, T>(h, src, dst);
     if (h->p.scheme == FDLBM_SCHEME_FD3)
-        return force ? launch_stream_typed<1, true, WALLS, T>(h, src, dst, n, done)
-                     : launch_stream_typed<1, false, WALLS, T>(h, src, dst, n, done);
-    return force ? launch_stream_typed<2, true, WALLS, T>(h, src, dst, n, done)
-                 : launch_stream_typed<2, false, WALLS, T>(h, src, dst, n, done);
+        return force ? launch_stream_typed<1, true, WALLS, T>(h, src, dst)
+                     : launch_stream_typed<1, false, WALLS, T>(h, src, dst);
+    return force ? launch_stream_typed<2, true, WALLS, T>(h, src, dst)
+                 : launch_stream_typed<2, false, WALLS, T>(h, src, dst);
 }
 
 template <typename T>
-cudaError_t launch_stream_boundary(fdlbm_s* h, const void* src, void* dst, int64_t n,
-                                   int* done) {
-    return h->p.boundary == FDLBM_BOUNDARY_WALLS_Y
-               ? launch_stream_stencil<true, T>(h, src, dst, n, done)
-               : launch_stream_stencil<false, T>(h, src, dst, n, done);
+cudaError_t launch_stream_boundary(fdlbm_s* h, const void* src, void* dst) {
+    return h->p.boundary == FDLBM_BOUNDARY_WALLS_Y ? launch_stream_stencil<true, T>(h, src, dst)
+                                                   : launch_stream_stencil<false, T>(h, src, dst);
 }
 
 }  // namespace
@@ -591,26 +490,13 @@ bool fd_stream_supported(const fdlbm_params& p) {
            p.nx % 8 == 0 && p.nx >= 256 && p.ny >= 16;
 }
 
-static cudaError_t launch_stream_any(fdlbm_s* h, const void* src, void* dst, int64_t n,
-                                     int* done) {
-    switch (h->p.storage) {
-        case FDLBM_STORAGE_F16: return launch_stream_boundary<__half>(h, src, dst, n, done);
-        case FDLBM_STORAGE_BF16:
-            return launch_stream_boundary<__nv_bfloat16>(h, src, dst, n, done);
-        case FDLBM_STORAGE_I16: return launch_stream_boundary<int16_t>(h, src, dst, n, done);
-        default: return launch_stream_boundary<float>(h, src, dst, n, done);
-    }
-}
-
 cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst) {
-    int done = 0;
-    return launch_stream_any(h, src, dst, 1, &done);
-}
-
-cudaError_t launch_fd_steps_stream(fdlbm_s* h, const void* src, void* dst, int64_t nsteps,
-                                   int* done) {
-    *done = 0;
-    return launch_stream_any(h, src, dst, nsteps, done);
+    switch (h->p.storage) {
+        case FDLBM_STORAGE_F16: return launch_stream_boundary<__half>(h, src, dst);
+        case FDLBM_STORAGE_BF16: return launch_stream_boundary<__nv_bfloat16>(h, src, dst);
+        case FDLBM_STORAGE_I16: return launch_stream_boundary<int16_t>(h, src, dst);
+        default: return launch_stream_boundary<float>(h, src, dst);
+    }
 }
 
 }  // namespace fdlbm

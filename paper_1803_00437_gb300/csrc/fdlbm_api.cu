@@ -127,13 +127,6 @@ bool compute_layout(const fdlbm_params& p, Layout* L) {
     off += L->reduce_bytes;
     L->off_flag = off;
     off += 256;
-    // completion records of the streaming kernel's work items (one int per
-    // item of at most ceil(nx / 120) strips x ceil(ny / 16) row segments),
-    // used when one launch advances several steps
-    L->off_items = off;
-    L->items_bytes = align_up(sizeof(int) * (size_t)((p.nx + 119) / 120) *
-                                  (size_t)((p.ny + 15) / 16), 256);
-    off += L->items_bytes;
     L->total = off;
     return true;
 }
@@ -240,9 +233,7 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
         delete h;
         return FDLBM_ERR_INVALID;
     }
-    h->item_epoch = 0;
-    if (cudaMemsetAsync(h->ws + h->L.off_items, 0, h->L.items_bytes, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->ws + h->L.off_flag, 0, sizeof(int), h->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(h->ws + h->L.off_flag, 0, sizeof(int), h->stream) != cudaSuccess) {
         cudaGetLastError();
         delete h;
         return FDLBM_ERR_CUDA;
@@ -355,22 +346,9 @@ int fdlbm_step(fdlbm_t* h, int64_t nsteps) {
     if (nsteps == 0) return FDLBM_OK;
     DeviceGuard g(h->device);
     if (!g.ok) return set_error(h, FDLBM_ERR_CUDA, "cannot select the handle's device");
-    for (int64_t n = 0; n < nsteps;) {
+    for (int64_t n = 0; n < nsteps; ++n) {
         void* src = state_ptr(h, h->cur);
         void* dst = state_ptr(h, 1 - h->cur);
-        if (!h->walls && h->p.scheme != FDLBM_SCHEME_MRT && fd_uses_stream(h) &&
-            nsteps - n >= 2) {
-            // several steps in one launch where the streaming kernel allows it
-            int done = 0;
-            cudaError_t e = launch_fd_steps_stream(h, src, dst, nsteps - n, &done);
-            h->launches += 1;
-            if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
-            if (done > 0) {
-                if (done & 1) h->cur = 1 - h->cur;
-                n += done;
-                continue;
-            }
-        }
         if (h->walls) {  // curved walls: the virtual fluid the step reads (Sec. 3-b)
             cudaError_t e = launch_walls_fill(h, src);
             h->launches += 1;
@@ -381,7 +359,6 @@ int fdlbm_step(fdlbm_t* h, int64_t nsteps) {
         h->launches += 1;
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
         h->cur = 1 - h->cur;
-        ++n;
     }
     if (h->walls) {
         cudaError_t e = launch_walls_fill(h, state_ptr(h, h->cur));
@@ -509,16 +486,13 @@ int64_t fdlbm_launch_count(const fdlbm_t* h) { return h ? h->launches : -1; }
 }  // extern "C"
 
 namespace fdlbm {
-bool fd_uses_stream(const fdlbm_s* h) {
+cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
     // the streaming kernel pays off once the lattice fills the GPU's warps
     constexpr int64_t kStreamMinNodes = 1 << 20;
     const bool big = (int64_t)h->p.nx * h->p.ny >= kStreamMinNodes;
-    return h->p.scheme != FDLBM_SCHEME_FD9 && h->fd_path != 1 && fd_stream_supported(h->p) &&
-           (big || h->fd_path == 2);
-}
-
-cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
-    if (fd_uses_stream(h)) return launch_fd_step_stream(h, src, dst);
+    if (h->p.scheme != FDLBM_SCHEME_FD9 && h->fd_path != 1 && fd_stream_supported(h->p) &&
+        (big || h->fd_path == 2))
+        return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }
 }  // namespace fdlbm

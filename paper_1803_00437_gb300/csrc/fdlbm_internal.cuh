@@ -134,8 +134,6 @@ struct Layout {
     size_t off_reduce;   // reduction scratch (doubles)
     size_t reduce_bytes;
     size_t off_flag;     // device status word
-    size_t off_items;    // streaming kernel: completion record per work item
-    size_t items_bytes;
     size_t total;
 };
 
@@ -163,8 +161,7 @@ struct fdlbm_s {
     char* ws;
     int cur;  // index of the current state copy
     int64_t launches;
-    int stream_plan_warps;  // resident CTAs of the streaming FD kernel (0: not queried)
-    uint32_t item_epoch;    // steps the multi-step streaming launches have recorded
+    int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
     int fd_path;            // 0: automatic, 1: tiled FD kernel, 2: streaming where it qualifies
     const void* walls;      // curved walls: device table of closure entries (NULL: none)
     int64_t walls_n;        // its number of entries
@@ -186,13 +183,7 @@ MrtCoeffs mrt_coeffs(const fdlbm_params& p);
 cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst);
-// Up to `nsteps` steps in one launch of the streaming kernel when its work
-// items fit on the GPU at once; *done receives the steps enqueued (0: none,
-// the caller falls back to one launch per step).
-cudaError_t launch_fd_steps_stream(fdlbm_s* h, const void* src, void* dst, int64_t nsteps,
-                                   int* done);
 bool fd_stream_supported(const fdlbm_params& p);
-bool fd_uses_stream(const fdlbm_s* h);
 cudaError_t launch_mrt_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,
                            void* dst);

@@ -23,6 +23,8 @@ def main(argv=None):
                     help="largest |value| of the i16 fixed-point storage")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=0, help="untimed steps before the timed ones")
+    ap.add_argument("--per-step", action="store_true",
+                    help="one fdlbm_step call per step")
     ap.add_argument("--nu", type=float, default=0.01)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--reduce", nargs="*", default=[],
@@ -41,14 +43,18 @@ def main(argv=None):
     lat.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(lat.stream)
-    lat.step(args.steps)
+    if args.per_step:
+        for _ in range(args.steps):
+            lat.step(1)
+    else:
+        lat.step(args.steps)
     e1.record(lat.stream)
     lat.sync()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     reductions = {w: [float(v) for v in lat.reduce(w)] for w in args.reduce}
     print(json.dumps({"side": n, "scheme": args.scheme, "storage": args.storage,
                       "steps": args.steps, "ms_per_step": round(ms, 4),
-                      "mlups": round(n * n / ms / 1e3, 1),
+                      "mlups": round(n * n / ms / 1e3, 1), "launches": lat.launches,
                       "max_u": float(lat.reduce("maxabs")[0]), "reductions": reductions}))
 
 

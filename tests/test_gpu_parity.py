@@ -429,35 +429,6 @@ def test_streaming_kernel_parity(oracle, scheme, shape):
     assert max_err(gpu, ref, amplitude(f)) <= TOL32
 
 
-@pytest.mark.parametrize("scheme,boundary,storage", [("fd5", "periodic", "f32"),
-                                                     ("fd3", "walls_y", "f32"),
-                                                     ("lwacm", "periodic", "f32"),
-                                                     ("fd5", "periodic", "i16")])
-def test_multistep_launch_equals_single_steps(scheme, boundary, storage):
-    """fdlbm_step(n) runs up to 64 steps in one cooperative launch of the
-    streaming kernel (each CTA waits only for its neighbouring items to
-    finish the previous step); the result must be the one of n launches of
-    one step, bit for bit, across a launch boundary (70 = 64 + 6 steps)."""
-    import torch
-    from paper_1803_00437_gb300 import fdlbm as F
-    nx, ny = 520, 83
-    f = as_f32(inputs.random_fields(nx, ny, 0.01, seed=12, rho_amp=2e-3))
-    kw = dict(boundary="walls_y", wall_xi=0.7, force=(1e-5, 0.0)) if boundary == "walls_y" else {}
-    cfg = _cfg(nx, ny, scheme, s_xx=_nu(0.02), s_e=1.5, flags=F.FLAG_STREAM, storage=storage,
-               storage_range=0.05 if storage == "i16" else 0.0, **kw)
-    many, lat = gpu_run(cfg, f, 70)
-    launches_many = lat.launches
-    one = F.Lattice(cfg)
-    one.init(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in f])
-    for _ in range(70):
-        one.step(1)
-    single = [t.cpu().numpy().astype(np.float64) for t in one.moments()]
-    one.sync()
-    for a, b in zip(many, single):
-        assert np.array_equal(a, b)
-    assert launches_many < one.launches  # the 70 steps took fewer launches
-
-
 @pytest.mark.parametrize("scheme,shape,xi", [("fd5", (256, 24), 0.5), ("fd5", (264, 37), 0.3),
                                               ("fd3", (256, 40), 1.0), ("fd5", (512, 64), 0.8),
                                               ("fd3", (264, 17), 0.3)])
