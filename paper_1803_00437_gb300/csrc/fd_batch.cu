@@ -160,6 +160,9 @@ struct BatchRowStep {
                                                const StreamCoeffs& kc, int lane, int k,
                                                Win& fm2, Win& fm1, Win& dm3, Win& dm2,
                                                Acc& acc) {
+        // five points: rows 0 and 1 of an item only wait in the ring for
+        // the window update of rows 2 and 3
+        if (WARM && R == 2 && k < R) return;
         const uint32_t pos = it.base + k;
         const int slot = pos & kSlotMask;
         const int col = 4 + 4 * lane;
@@ -188,6 +191,10 @@ struct BatchRowStep {
                 cuy[0] = mul2(cuy[0], fac);
                 cuy[1] = mul2(cuy[1], fac);
             }
+        }
+        if (WARM && R > 0 && k < 2 * R) {  // the window only: no output needs this row
+            window_row<R>(nr, nux, nuy, cdr, cux, cuy, fm2, dm3);
+            return;
         }
         float2 odr[2], oux[2], ouy[2];
         stream_row<R, FORCE>(nr, nux, nuy, cdr, cux, cuy, kc, fm2, fm1, dm3, dm2, acc, odr, oux,

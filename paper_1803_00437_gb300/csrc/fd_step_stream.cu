@@ -191,20 +191,57 @@ __device__ __forceinline__ uint32_t release_inc(uint32_t* counter, uint32_t last
     return old;
 }
 
-// The warp has read ring row m for the last time: count its release; the
-// CTA's last release refills the slot with row m + kSlots.  Lane 0 only;
-// the item's description is read from shared memory (it is needed only
-// here, so it is not held in registers through the row loop).
+// One field of ring row k (position pos) into its slot, by the calling lane.
 template <bool WALLS, typename T, int W>
-__device__ __forceinline__ void release_row(const StreamArgs& a, const Item* s_item,
-                                            uint32_t base, int m) {
-    const int nrows = s_item->nrows, active = s_item->active;
-    if (m < 0 || m + kSlots >= nrows) return;  // no refill follows this row
-    const uint32_t pos = base + m;
-    if (release_inc(Ring<W, T>::count(pos & kSlotMask), active - 1) == (uint32_t)(active - 1)) {
-        const Item it = *s_item;
-        issue_row<WALLS, T, W>(a, it, pos + kSlots, m + kSlots);
+__device__ __forceinline__ void issue_field(const StreamArgs& a, const Item& it, uint32_t pos,
+                                            int k, int f) {
+    using ring = Ring<W, T>;
+    const int slot = pos & kSlotMask;
+    int r = it.row_first + k;
+    if (!WALLS) {
+        if (r < 0) r += a.ny;
+        if (r >= a.ny) r -= a.ny;
+    } else if (r < 0 || r >= a.ny) {
+        r = f == 0 ? wall_edge(r, a.ny) : wall_ref(r, a.ny, a.xi);
     }
+    fence_proxy_async_smem();
+    const T* rowp = static_cast<const T*>(a.src) + f * a.plane + (size_t)r * a.pitch;
+    T* d = reinterpret_cast<T*>(g_smem) + ((size_t)slot * 3 + f) * ring::cols;
+    uint64_t* bar = ring::full(slot);
+    tma_load_1d(d, rowp + it.x0, it.first * sizeof(T), bar);
+    if (it.first < (int)ring::cols)
+        tma_load_1d(d + it.first, rowp, (ring::cols - it.first) * sizeof(T), bar);
+}
+
+// The warp has read ring rows m0 and m0 + 1 for the last time.  Lanes 0 and
+// 1 count the two releases (in parallel); a row whose release is the CTA's
+// last is refilled with the row kSlots ahead: its lane arms the barrier,
+// then three lanes copy one field each.  The item's description is read
+// from shared memory (it is needed only here, so it is not held in
+// registers through the row loop).
+template <bool WALLS, typename T, int W>
+__device__ __forceinline__ void release_pair(const StreamArgs& a, const Item* s_item,
+                                             uint32_t base, int m0, int lane) {
+    using ring = Ring<W, T>;
+    const int nrows = s_item->nrows, active = s_item->active;
+    const int m = m0 + (lane & 1);
+    bool last = false;
+    if (lane < 2 && m >= 0 && m + kSlots < nrows)  // otherwise no refill follows the row
+        last = release_inc(ring::count((base + m) & kSlotMask), active - 1) ==
+               (uint32_t)(active - 1);
+    const uint32_t refill = __ballot_sync(kFull, last);  // bit j: row m0 + j
+    if (refill == 0) return;
+    const Item it = *s_item;
+    if (last) {
+        const uint32_t pos = base + m + kSlots;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(ring::full(pos & kSlotMask), 3u * ring::cols * sizeof(T));
+        *ring::last(pos & kSlotMask) = (int)pos;
+    }
+    __syncwarp();
+    const int j = lane >= 3 ? 1 : 0;
+    if (lane < 6 && ((refill >> j) & 1u))
+        issue_field<WALLS, T, W>(a, it, base + m0 + j + kSlots, m0 + j + kSlots, lane - 3 * j);
 }
 
 template <int R, bool FORCE, bool WALLS, typename T, int W>
@@ -221,6 +258,9 @@ struct RowStep {
                                                Win& fm1, Win& dm3, Win& dm2, Acc& acc) {
         constexpr uint32_t slot_bytes = Ring<W, T>::slot_bytes;
         constexpr uint32_t field_bytes = Ring<W, T>::field_bytes;
+        // five points: rows 0 and 1 of an item only wait in the ring for
+        // the window update of rows 2 and 3
+        if (WARM && R == 2 && k < R) return;
         const uint32_t pos = base + k;
         const uint32_t row = lane_off + (pos & kSlotMask) * slot_bytes;
         float2 nr[2], nux[2], nuy[2];
@@ -256,6 +296,10 @@ struct RowStep {
                     cuy[1] = mul2(cuy[1], fac);
                 }
             }
+        }
+        if (WARM && R > 0 && k < 2 * R) {  // the window only: no output needs this row
+            window_row<R>(nr, nux, nuy, cdr, cux, cuy, fm2, dm3);
+            return;
         }
         float2 odr[2], oux[2], ouy[2];
         stream_row<R, FORCE>(nr, nux, nuy, cdr, cux, cuy, a.k, fm2, fm1, dm3, dm2, acc, odr, oux,
@@ -304,10 +348,7 @@ __device__ __forceinline__ bool warp_item(const StreamArgs& a, const Item* s_ite
         // the centre rows of these two steps (k - R, k + 1 - R) are read for
         // the last time: release their slots
         __syncwarp();
-        if (lane == 0) {
-            release_row<WALLS, T, W>(a, s_item, base, k - R);
-            release_row<WALLS, T, W>(a, s_item, base, k + 1 - R);
-        }
+        release_pair<WALLS, T, W>(a, s_item, base, k - R, lane);
     }
     if (k < nrows) {
         if (!__all_sync(kFull, row_landed<W, T>(base + k))) return false;

@@ -278,6 +278,36 @@ struct Acc {
 };
 
 
+// The y window's update alone, for the first rows of an item (k < 2R),
+// whose centre rows' populations reach no output row: three points keep the
+// new row (fm2 takes it); five points keep n1 = f(c) - f(c + 2) of the
+// centre row c = k - 2 and the new row (dm3 takes it), needed from k = R on.
+template <int R>
+__device__ __forceinline__ void window_row(const float2 nr[2], const float2 nux[2],
+                                           const float2 nuy[2], const float2 cdr[2],
+                                           const float2 cux[2], const float2 cuy[2], Win& fm2,
+                                           Win& dm3) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float2 jx = fma2(nr[h], nux[h], nux[h]), jy = fma2(nr[h], nuy[h], nuy[h]);
+        const float2 pxy = mul2(jx, nuy[h]), pyy = mul2(jy, nuy[h]);
+        if (R == 1) {
+            fm2.v[W_R][h] = nr[h];
+            fm2.v[W_JX][h] = jx;
+            fm2.v[W_JY][h] = jy;
+            fm2.v[W_PXY][h] = pxy;
+            fm2.v[W_PYY][h] = pyy;
+        } else {
+            const float2 cjx = fma2(cdr[h], cux[h], cux[h]), cjy = fma2(cdr[h], cuy[h], cuy[h]);
+            dm3.v[W_R][h] = sub2(cdr[h], nr[h]);
+            dm3.v[W_JX][h] = sub2(cjx, jx);
+            dm3.v[W_JY][h] = sub2(cjy, jy);
+            dm3.v[W_PXY][h] = sub2(mul2(cjx, cuy[h]), pxy);
+            dm3.v[W_PYY][h] = sub2(mul2(cjy, cuy[h]), pyy);
+        }
+    }
+}
+
 // One row of the streaming step, shared by the single-lattice and the batched
 // kernels.  In: the new field row k (nr, nux, nuy; channel rows already
 // scaled) and, for R > 0, the centre row c = k - R (cdr, cux, cuy; zeros
