@@ -60,6 +60,9 @@ def parse_args():
     ap.add_argument("--batched-lattices", type=int, default=1024,
                     help="lattices of the batched sample in the default line")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=300,
+                    help="requests of the serving sample in the default line")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -385,6 +388,15 @@ def run_ours(args):
                                   local)
         batched["value"] = round(all_sum(batched["value"], world, dev), 1)
 
+    # served requests beside them: the first requests of the specified stream
+    # (Poisson arrivals at 200/s, an overload), their latencies and solves/s
+    serving = None
+    if not args.no_serving:
+        from paper_1803_00437_gb300 import serve
+        torch.cuda.empty_cache()
+        serving = serve.measure_stream(args.serving_requests, device=dev)
+        torch.cuda.empty_cache()
+
     peak, peak_kind = hbm_peak()
 
     def roofline(scheme, kernel):
@@ -415,9 +427,18 @@ def run_ours(args):
         "lwacm": {"value": round(lw_value, 1), "unit": "MLUPS",
                   "ms_per_step": round(lw_ms, 5), "roofline": roofline("lwacm", "lwacm_step")},
         "gpu_launches": int(sum(r["launches"] for r in results.values())
-                            + (batched["gpu_launches"] if batched else 0)),
+                            + (batched["gpu_launches"] if batched else 0)
+                            + (serving["gpu_launches"] if serving else 0)),
         "clocks": clocks, "health": health, "e2e": e2e,
     }
+    if serving:
+        serving["workload"] = (f"the first {args.serving_requests} requests of the serving stream "
+                               "(Poisson 200/s, sides log-U[64,4096], steps log-U[100,20000], "
+                               "shear wave / 1-4 modes / Poiseuille, nu U[0.002,0.1]), FD-LBM "
+                               "five-point FP32, 80 GB HBM budget, continuous batching")
+        serving["unit"] = "solves/s"
+        serving["value"] = serving["solves_per_s"]
+        line["serving"] = serving
     if batched:
         batched["workload"] = (f"{batched['lattices']} periodic lattices of the batched workload "
                                "(sides U{32..512}, nu U[0.002,0.1], one transverse mode A=1e-3 "

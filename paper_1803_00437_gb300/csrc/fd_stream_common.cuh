@@ -199,13 +199,12 @@ __device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, fl
     const float2 udr = fma2(uy, dyr, mul2(ux, dxr));
     const float2 ke36 =
         fma2(sp(k.em2), udr, mul2(fma2(sp(k.e6), u2, sp(k.e2)), add2(dxjx, dyjy)));
-    // K_XX = -(2/3) a_xx [ux Ex - uy Ey - (dxJx - dyJy)]
-    const float2 kxx = mul2(sp(k.xm23), fma2(ux, ex, fma2(nuy, ey, sub2(dyjy, dxjx))));
-    // K_XY = (1/3) a_xx [(dxJy + dyJx) - (ux Ey + uy Ex)]
-    const float2 kxy = mul2(sp(k.x13), sub2(add2(dxjy, dyjx), fma2(ux, ey, mul2(uy, ex))));
+    // XX = Pxx - Pyy + K_XX, K_XX = -(2/3) a_xx [ux Ex - uy Ey - (dxJx - dyJy)]
+    const float2 xx =
+        fma2(sp(k.xm23), fma2(ux, ex, fma2(nuy, ey, sub2(dyjy, dxjx))), sub2(pxx, pyy));
+    // XY = Pxy + K_XY, K_XY = (1/3) a_xx [(dxJy + dyJx) - (ux Ey + uy Ex)]
+    const float2 xy = fma2(sp(k.x13), sub2(add2(dxjy, dyjx), fma2(ux, ey, mul2(uy, ex))), pxy);
     const float2 ru2_12 = mul2(add2(pxx, pyy), sp(1.f / 12.f));
-    const float2 xx = add2(sub2(pxx, pyy), kxx);
-    const float2 xy = add2(pxy, kxy);
     const float2 axis = sub2(fma2(dr, sp(1.f / 9.f), ru2_12), ke36);
     const float2 diag = fma2(sp(2.f), ke36, fma2(dr, sp(1.f / 36.f), ru2_12));
     g[0] = fma2(sp(-4.f), add2(axis, diag), dr);

@@ -194,6 +194,23 @@ def latency_stats(done, wall: float):
             "node_updates": int(sum(r.work for r in done))}
 
 
+def measure_stream(n: int, rate: float = 200.0, hbm_budget: int = 80 << 30, device=None):
+    """Serve the first n requests of the specified stream (Poisson arrivals at
+    `rate` per second, sides log-uniform in [64, 4096], 100-20000 steps,
+    shear wave / 1-4 modes / Poiseuille channel, nu U[0.002, 0.1]) under an
+    HBM budget; returns the latency statistics and the sustained MLUPS."""
+    reqs = make_requests(n, rate, inputs.seed_for(4))
+    srv = Server(hbm_budget=hbm_budget, max_slots=1024, max_side=4096, device=device)
+    t0 = time.perf_counter()
+    done = srv.serve(reqs)
+    wall = time.perf_counter() - t0
+    out = latency_stats(done, wall)
+    out["mlups"] = round(srv.work_done / wall / 1e6, 1)
+    out["gpu_launches"] = int(srv.batch.launches)
+    srv.batch.close()
+    return out
+
+
 def bench_main(args):
     """bench.py --workload serving: the Poisson stream (mean 200 requests/s) of
     mixed FD-LBM requests, 80 GB HBM budget; then the same mix at 25/50/75 %
