@@ -421,33 +421,42 @@ struct Plan {
 // an mbarrier arrival with its pending count: all within 1 %).
 constexpr int kWarps = 2;
 
-// Segment length that balances the waves: the critical path is
-// ceil(items / resident CTAs) * (segment + halo rows).
-Plan make_plan(int nx, int ny, int R, int W, int resident_ctas) {
+// Row segments of equal length (about 16 rows or more).  A segment streams
+// rows beyond its own (2 whose populations cross its ends, and 2R that only
+// fill the y window, at a fraction of a row's cost), and a launch ends with
+// a tail while its last CTAs finish.  With w = items / resident CTAs (the
+// waves) the step time follows
+//   (segment rows + c) (w + a),
+// c = 0.5 + 2R extra rows (2 for LW-ACM, R = 0) and a = 0.2 of an item's
+// time, except for LW-ACM with FP32 storage, which runs near the memory
+// bound and whose extra rows mostly come from L2: c = 0.5, a = 0.4.  This
+// fits, within
+// 1.3 %, step times measured on GB300 over segment counts (FD-5 on 4096^2,
+// 8192^2 and 16384^2; FD-3, LW-ACM and LW-ACM with FP16 storage on 8192^2).
+// The minimum lies at 3-7 waves for the finite-difference steps on the large
+// lattices (8192^2 FD-5: 128 segments of 64 rows, 206 GLUPS, against 192 for
+// one wave of 241-row segments) and at 16-row segments for LW-ACM (275
+// GLUPS against 243 for 119-row segments).
+Plan make_plan(int nx, int ny, int R, int W, int resident_ctas, int elem_bytes) {
     const int nstrips = (nx + kStrip - 1) / kStrip;
     Plan best{W, (nstrips + W - 1) / W, ny, 1, 0, 0};
-    best.nitems = best.ncstrips;
-    long long best_cost = -1;
-    for (int s = 16; s <= ny; s += (s < 128 ? 8 : 16)) {
+    const bool near_memory_bound = R == 0 && elem_bytes == 4;
+    const double c = near_memory_bound ? 0.5 : (R == 0 ? 2.0 : 0.5 + 2.0 * R);
+    const double a = near_memory_bound ? 0.4 : 0.2;
+    double best_cost = -1.0;
+    const int max_segs = (ny + 15) / 16;
+    for (int n = 1; n <= max_segs; ++n) {
+        const int s = (ny + n - 1) / n;
         const int nsegs = (ny + s - 1) / s;
-        const int items = best.ncstrips * nsegs;
-        const long long waves = (items + resident_ctas - 1) / resident_ctas;
-        const long long cost = waves * (long long)(s + 2 + 2 * R);
-        if (best_cost < 0 || cost < best_cost) {
+        if (nsegs != n) continue;  // the same segments as a smaller count
+        const double waves = (double)best.ncstrips * nsegs / resident_ctas;
+        const double cost = (s + c) * (waves + a);
+        if (best_cost < 0.0 || cost < best_cost) {
             best_cost = cost;
             best.seg_rows = s;
             best.nsegs = nsegs;
-            best.nitems = items;
         }
     }
-    if (ny < 16) {
-        best.seg_rows = ny;
-        best.nsegs = 1;
-        best.nitems = best.ncstrips;
-    }
-    // the same number of segments, of equal length (rather than a short last one)
-    best.seg_rows = (ny + best.nsegs - 1) / best.nsegs;
-    best.nsegs = (ny + best.seg_rows - 1) / best.seg_rows;
     best.nitems = best.ncstrips * best.nsegs;
     best.blocks = best.nitems;
     return best;
@@ -468,7 +477,7 @@ cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, W * 32, smem);
         h->stream_plan_warps = std::max(1, sms * per_sm);  // resident CTAs
     }
-    const Plan plan = make_plan(h->p.nx, h->p.ny, R, W, h->stream_plan_warps);
+    const Plan plan = make_plan(h->p.nx, h->p.ny, R, W, h->stream_plan_warps, (int)sizeof(T));
     StreamArgs a;
     a.src = src;
     a.dst = dst;
