@@ -503,7 +503,6 @@ cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
     a.k.hfy = (float)(0.5 * h->p.force_y);
     const double nu = (1.0 / h->p.s_xx - 0.5) / 3.0;  // LW-ACM (Sec. 1-b)
     a.k.lw_t = (float)(2.0 * nu);
-    a.k.lw_s = a.k.lw_t * 0.25f;
     a.q = quant_of(h->p);
     a.status = reinterpret_cast<int*>(h->ws + h->L.off_flag);
     kernel<<<plan.blocks, W * 32, smem, h->stream>>>(a);

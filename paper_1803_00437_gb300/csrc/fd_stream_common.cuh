@@ -147,7 +147,7 @@ struct StreamCoeffs {
     float e6, e2, em2;  // theta_E terms, times (1 - 1/s_e) / (36 scale)
     float xm23, x13;    // -2/3 and 1/3, times (1 - 1/s_xx) / scale (theta_XX, theta_XY)
     float hfx, hfy;            // half of the body force
-    float lw_t, lw_s;          // LW-ACM: 2 nu and nu / 2 (exactly lw_t / 4)
+    float lw_t;                // LW-ACM: 2 nu
 };
 
 // x-derivative (scaled by 2 or 8) at the 4 columns of this lane.
@@ -174,7 +174,8 @@ __device__ __forceinline__ void deriv_x(const float2 v[2], float2 d[2]) {
 // u2 = |u|^2, the moments of the table of Sec. 2 substituted into M^-1 give
 //   g0 = dr - 4 (axis + diag)            (so that sum g = dr, unbiased)
 //   axis = dr/9 + rho u2/12 - K_E/36,     diag = dr/36 + rho u2/12 + K_E/18
-//   tx = (jx + Jx)/6, sx = (jx - 2 tx)/4 (so that sum c g = jx, unbiased)
+//   tx = (jx + Jx)/6, sx = (jx - 2 tx)/4 (so that sum c g = jx, unbiased),
+//   carried as 2 tx and 4 sx (exact scalings, the same roundings)
 //   g1,3 = axis + XX/4 +- tx,  g2,4 = axis - XX/4 +- ty,
 //   g5,7 = diag + XY/4 +- (sx + sy),  g6,8 = diag - XY/4 +- (sy - sx),
 // with jx = Jx + F/2 (Strang) and q = -J, epsilon at equilibrium.
@@ -208,29 +209,30 @@ __device__ __forceinline__ void reconstruct2(float2 dr, float2 ux, float2 uy, fl
     const float2 axis = sub2(fma2(dr, sp(1.f / 9.f), ru2_12), ke36);
     const float2 diag = fma2(sp(2.f), ke36, fma2(dr, sp(1.f / 36.f), ru2_12));
     g[0] = fma2(sp(-4.f), add2(axis, diag), dr);
-    float2 tx, ty, jx = Jx, jy = Jy;
+    // t2 = 2 t, s4 = 4 s: fl(2/3) = 2 fl(1/3) and the factors 1/2, 1/4 below
+    // are exact, so every population has the roundings of the t, s form
+    float2 tx2, ty2, jx = Jx, jy = Jy;
     if (FORCE) {
         jx = add2(Jx, sp(k.hfx));
         jy = add2(Jy, sp(k.hfy));
-        tx = mul2(add2(jx, Jx), sp(1.f / 6.f));
-        ty = mul2(add2(jy, Jy), sp(1.f / 6.f));
+        tx2 = mul2(add2(jx, Jx), sp(1.f / 3.f));
+        ty2 = mul2(add2(jy, Jy), sp(1.f / 3.f));
     } else {
-        tx = mul2(Jx, sp(1.f / 3.f));
-        ty = mul2(Jy, sp(1.f / 3.f));
+        tx2 = mul2(Jx, sp(2.f / 3.f));
+        ty2 = mul2(Jy, sp(2.f / 3.f));
     }
-    const float2 sx = mul2(fma2(sp(-2.f), tx, jx), sp(0.25f));
-    const float2 sy = mul2(fma2(sp(-2.f), ty, jy), sp(0.25f));
+    const float2 sx4 = sub2(jx, tx2), sy4 = sub2(jy, ty2);
     const float2 ax = fma2(xx, sp(0.25f), axis), ay = fma2(xx, sp(-0.25f), axis);
     const float2 dp = fma2(xy, sp(0.25f), diag), dm = fma2(xy, sp(-0.25f), diag);
-    const float2 spp = add2(sx, sy), smm = sub2(sy, sx);
-    g[1] = add2(ax, tx);
-    g[3] = sub2(ax, tx);
-    g[2] = add2(ay, ty);
-    g[4] = sub2(ay, ty);
-    g[5] = add2(dp, spp);
-    g[7] = sub2(dp, spp);
-    g[6] = add2(dm, smm);
-    g[8] = sub2(dm, smm);
+    const float2 spp4 = add2(sx4, sy4), smm4 = sub2(sy4, sx4);
+    g[1] = fma2(tx2, sp(0.5f), ax);
+    g[3] = fma2(tx2, sp(-0.5f), ax);
+    g[2] = fma2(ty2, sp(0.5f), ay);
+    g[4] = fma2(ty2, sp(-0.5f), ay);
+    g[5] = fma2(spp4, sp(0.25f), dp);
+    g[7] = fma2(spp4, sp(-0.25f), dp);
+    g[6] = fma2(smm4, sp(0.25f), dm);
+    g[8] = fma2(smm4, sp(-0.25f), dm);
 }
 
 // LW-ACM reconstruction (Sec. 1-b, Eq. 3) of two columns.  After the
@@ -256,17 +258,17 @@ __device__ __forceinline__ void reconstruct_lw2(float2 dr, float2 Jx, float2 Jy,
     const float2 d = fma2(S, sp(1.f / 12.f), mul2(dr, sp(1.f / 36.f)));
     const float2 dp = fma2(pxy, sp(0.25f), d), dm = fma2(pxy, sp(-0.25f), d);
     const float2 tx = mul2(Jx, sp(k.lw_t)), ty = mul2(Jy, sp(k.lw_t));
-    const float2 sx = mul2(Jx, sp(k.lw_s)), sy = mul2(Jy, sp(k.lw_s));
-    const float2 spp = add2(sx, sy), smm = sub2(sy, sx);
+    // s = t / 4 exactly: the diagonal populations take (ty +- tx) / 4
+    const float2 spp4 = add2(tx, ty), smm4 = sub2(ty, tx);
     g[0] = fma2(sp(-2.f), add2(add2(ax, ay), add2(dp, dm)), dr);
     g[1] = add2(ax, tx);
     g[3] = sub2(ax, tx);
     g[2] = add2(ay, ty);
     g[4] = sub2(ay, ty);
-    g[5] = add2(dp, spp);
-    g[7] = sub2(dp, spp);
-    g[6] = add2(dm, smm);
-    g[8] = sub2(dm, smm);
+    g[5] = fma2(spp4, sp(0.25f), dp);
+    g[7] = fma2(spp4, sp(-0.25f), dp);
+    g[6] = fma2(smm4, sp(0.25f), dm);
+    g[8] = fma2(smm4, sp(-0.25f), dm);
 }
 
 // Per-lane gather state, in column pairs: destination row c (partial, "A")
