@@ -543,6 +543,7 @@ def measure_batched(n_lattices: int, steps: int, warmup: int, dev_index: int = 0
     out = {"value": round(nodes * steps / ms / 1e3, 1), "unit": "MLUPS", "steps": steps,
            "warmup": warmup, "ms_per_step": round(ms / steps, 4), "lattices": len(lats),
            "total_nodes": nodes, "rows_per_item": seg,
+           "narrow_last_strips": bool(b.tuned[1]),
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
                         "peak_spec": SPEC_HBM_GBS, "frac_spec": round(gbs / SPEC_HBM_GBS, 4),
@@ -570,7 +571,9 @@ def run_batched(args):
         "config": {"workload": f"{r['lattices']} periodic lattices, sides U{{32..512}}, nu "
                                "U[0.002,0.1], one transverse mode A=1e-3 each, FD-LBM five-point "
                                "FP32", "lattices": r["lattices"], "total_nodes": r["total_nodes"],
-                   "rows_per_item": r["rows_per_item"], "l2": "state larger than L2: no flush"},
+                   "rows_per_item": r["rows_per_item"],
+                   "narrow_last_strips": r["narrow_last_strips"],
+                   "l2": "state larger than L2: no flush"},
         "roofline": r["roofline"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "health": r["health"],
     }

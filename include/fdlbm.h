@@ -265,9 +265,17 @@ int fdlbm_batch_reduce(fdlbm_batch_t* b, int32_t slot, int32_t what, const doubl
 /* Wait for the batch's stream; reports a device-side timeout. */
 int fdlbm_batch_sync(fdlbm_batch_t* b);
 /* Tuning knobs (chosen by the autotuner in the Python layer): rows per work
- * item (>= 8) and persistent CTAs (0 = one wave of resident CTAs). */
+ * item (>= 8), persistent CTAs (0 = one wave of resident CTAs), and the strip
+ * form of each lattice's last strip: with narrow strips on (1, the default)
+ * a last strip of at most 56 columns runs on lanes of 2 columns (a warp
+ * covers 56 output columns) instead of 4 (120), so that fewer columns are
+ * computed for the ones stored; off (0): every strip on 4-column lanes.
+ * Both forms compute the same populations in the same order (Sec. 2, Eq. 2).
+ * Settings apply from the next fdlbm_batch_step.  FDLBM_ERR_INVALID for a
+ * NULL handle or an out-of-range value. */
 int fdlbm_batch_set_segment_rows(fdlbm_batch_t* b, int32_t rows);
 int fdlbm_batch_set_grid(fdlbm_batch_t* b, int32_t ctas);
+int fdlbm_batch_set_narrow_strips(fdlbm_batch_t* b, int32_t on);
 /* Message of the batch's last failed call (owned by the batch; "NULL handle"
  * for b == NULL). */
 const char* fdlbm_batch_last_error(const fdlbm_batch_t* b);

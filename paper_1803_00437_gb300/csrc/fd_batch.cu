@@ -1,7 +1,7 @@
 // fd_batch.cu -- batched FD-LBM steps (Sec. 2, Eq. 2) for many independent
 // lattices of any size (sides >= 16), each periodic or a channel with walls
-// in y, advanced by one persistent kernel per step; a run of steps is
-// captured once in a CUDA graph and replayed.
+// in y, advanced by persistent kernels (one per item list) per step; a run
+// of steps is captured once in a CUDA graph and replayed.
 //
 // Storage.  Every slot lives in a caller-owned arena: two copies (ping-pong)
 // of 3 planes (rho - 1, ux, uy), rows of `pitch` floats holding the logical
@@ -15,6 +15,10 @@
 // Work.  An item is (slot, 120-column strip, row segment), processed by one
 // warp exactly like the single-lattice streaming kernel; warps take items
 // from an atomic counter (one counter per step of the captured run).  A
+// lattice's last strip of at most 56 columns may run on 2-column lanes (a
+// narrow strip); narrow items form a list of their own, advanced by a second
+// kernel after the first in every step, so that no SM runs both forms' code
+// at once (together they overflow the instruction cache).  A
 // per-slot descriptor carries the slot's size, relaxation factors, force,
 // which copy holds the state, and how many steps of the run the slot takes,
 // so lattices of different viscosity and remaining step count share the
@@ -24,6 +28,7 @@
 
 #include <algorithm>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "fd_stream_common.cuh"
@@ -38,6 +43,10 @@ constexpr int kWarpsPerBlock = 1;  // one-warp CTAs, 16 resident per SM (128 reg
 constexpr int kMinBlocks = 16;
 constexpr int kStrip = 120;
 constexpr int kLoadCols = 136;
+// Narrow strips (2-column lanes) for a lattice's last strip when it holds at
+// most 56 columns: 64 columns in the lanes plus 8 staged for alignment.
+constexpr int kNarrowStrip = 56;
+constexpr int kNarrowCols = 72;
 constexpr int kSlots = 8;
 constexpr int kSlotMask = kSlots - 1;
 constexpr int kGhost = 8;
@@ -49,7 +58,7 @@ constexpr int kRedBlocks = 256;
 struct Lat {
     long long off[2];  // element offsets of the two state copies in the arena
     int nx, ny, pitch, walls;
-    int nstrips, seg_rows, nsegs, item_begin;
+    int nstrips, seg_rows, nsegs;
     int stop;          // steps this slot takes in the current run (0: idle)
     int cur;           // copy holding the state at the start of the run
     float xi, pad;
@@ -59,10 +68,10 @@ struct Lat {
 struct Args {
     float* arena;
     const Lat* lats;
-    const int* item_slot;
-    const int* nitems;  // device: number of items (changes without re-capture)
+    const int2* items;  // (slot, strip + segment x strips): the wide list, then the narrow one
+    const int* counts;  // device: items in the two lists (change without re-capture)
     int step;           // step index within the run
-    int* counter;    // work counter of this step
+    int* counter;       // work counter of this step and list
     int* status;
 };
 
@@ -83,6 +92,7 @@ struct Item {
     float* dst;
     size_t plane;
     bool lane_stores;
+    int cols;          // staged columns per field: kLoadCols, or kNarrowCols (narrow strip)
     uint32_t base;
 };
 
@@ -116,7 +126,7 @@ __device__ __forceinline__ void issue_rows(const Ring& ring, const Item& it, int
     if (lane < count) {
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(&ring.bars[(it.base + k0 + lane) & kSlotMask],
-                              3u * kLoadCols * sizeof(float));
+                              3u * it.cols * sizeof(float));
     }
     __syncwarp();
     if (lane < 3 * count) {
@@ -129,7 +139,7 @@ __device__ __forceinline__ void issue_rows(const Ring& ring, const Item& it, int
         const int r = f == 0 ? rrho : ru;
         fence_proxy_async_smem();
         const float* rowp = it.src + f * it.plane + (size_t)r * it.pitch + it.strip0;
-        tma_load_1d(slot_field(ring, slot, f), rowp, kLoadCols * sizeof(float), &ring.bars[slot]);
+        tma_load_1d(slot_field(ring, slot, f), rowp, it.cols * sizeof(float), &ring.bars[slot]);
     }
 }
 
@@ -231,7 +241,121 @@ struct BatchRowStep {
     }
 };
 
+// The narrow-strip row step: lane L holds logical columns strip0 - 4 + 2L and
+// the next one (ring columns 4 + 2L), lanes 2..29 store.
 template <int R, bool FORCE>
+struct BatchRowStep1 {
+    template <bool WARM>
+    static __device__ __forceinline__ void run(const Ring& ring, const Item& it,
+                                               const StreamCoeffs& kc, int lane, int k,
+                                               Win1& fm2, Win1& fm1, Win1& dm3, Win1& dm2,
+                                               Acc1& acc) {
+        if (WARM && R == 2 && k < R) return;
+        const uint32_t pos = it.base + k;
+        const int slot = pos & kSlotMask;
+        const int col = 4 + 2 * lane;
+        const float2 nr = *reinterpret_cast<const float2*>(slot_field(ring, slot, 0) + col);
+        float2 nux = *reinterpret_cast<const float2*>(slot_field(ring, slot, 1) + col);
+        float2 nuy = *reinterpret_cast<const float2*>(slot_field(ring, slot, 2) + col);
+        if (it.walls) {
+            const float2 fac = sp(row_factor(it, it.row_first + k));
+            nux = mul2(nux, fac);
+            nuy = mul2(nuy, fac);
+        }
+        const int cslot = (pos - R) & kSlotMask;
+        float2 cdr = sp(0.f), cux = sp(0.f), cuy = sp(0.f);
+        if (!WARM || k >= R) {
+            if (R == 2) cdr = *reinterpret_cast<const float2*>(slot_field(ring, cslot, 0) + col);
+            cux = *reinterpret_cast<const float2*>(slot_field(ring, cslot, 1) + col);
+            cuy = *reinterpret_cast<const float2*>(slot_field(ring, cslot, 2) + col);
+            if (it.walls) {
+                const float2 fac = sp(row_factor(it, it.row_first + k - R));
+                cux = mul2(cux, fac);
+                cuy = mul2(cuy, fac);
+            }
+        }
+        if (WARM && k < 2 * R) {  // the window only: no output needs this row
+            window_row1<R>(nr, nux, nuy, cdr, cux, cuy, fm2, dm3);
+            return;
+        }
+        float2 odr, oux, ouy;
+        stream_row1<R, FORCE>(nr, nux, nuy, cdr, cux, cuy, kc, fm2, fm1, dm3, dm2, acc, odr, oux,
+                              ouy);
+        if ((!WARM || k >= warm_rows<R>()) && it.lane_stores) {
+            const int c0 = it.strip0 - 4 + 2 * lane;  // logical column of this lane
+            const size_t row = (size_t)(it.yb + k - 2 * R - 2) * it.pitch;
+            float* d0 = it.dst + row;
+            const float v[3][2] = {{odr.x, odr.y}, {oux.x, oux.y}, {ouy.x, ouy.y}};
+            if (c0 + 1 < it.nx) {
+#pragma unroll
+                for (int f = 0; f < 3; ++f)
+                    *reinterpret_cast<float2*>(d0 + f * it.plane + c0 + kGhost) =
+                        make_float2(v[f][0], v[f][1]);
+            } else {  // the lattice's last column is the pair's first
+#pragma unroll
+                for (int f = 0; f < 3; ++f) d0[f * it.plane + c0 + kGhost] = v[f][0];
+            }
+            // periodic ghost columns of the destination copy
+            if (c0 < kGhost || c0 + 2 > it.nx - kGhost) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int c = c0 + j;
+                    if (c >= it.nx) continue;
+                    if (c >= it.nx - kGhost) {
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) d0[f * it.plane + c - it.nx + kGhost] = v[f][j];
+                    }
+                    if (c < kGhost) {
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) d0[f * it.plane + c + it.nx + kGhost] = v[f][j];
+                    }
+                }
+            }
+        }
+    }
+};
+
+// The rows of one item for one warp, in the wide (4-column lanes) or the
+// narrow form; false if a copy did not land in time.  `issued` counts the
+// ring positions whose copies were issued, `k` returns the rows consumed.
+template <int R, bool FORCE, bool NARROW>
+__device__ __forceinline__ bool item_rows(const Ring& ring, const Item& it, const StreamCoeffs& kc,
+                                          int lane, uint32_t& issued, int& k) {
+    using W = typename std::conditional<NARROW, Win1, Win>::type;
+    using A = typename std::conditional<NARROW, Acc1, Acc>::type;
+    using Step = typename std::conditional<NARROW, BatchRowStep1<R, FORCE>,
+                                           BatchRowStep<R, FORCE>>::type;
+    W w0 = {}, w1 = {}, w2 = {}, w3 = {};
+    A acc = {};
+    k = 0;
+    for (; k + 1 < it.nrows; k += 2) {
+        const bool l0 = row_landed(ring, it, k), l1 = row_landed(ring, it, k + 1);
+        if (!__all_sync(kFull, l0 && l1)) return false;
+        if (k >= warm_rows<R>()) {
+            Step::template run<false>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+            Step::template run<false>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
+        } else {
+            Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+            Step::template run<true>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
+        }
+        __syncwarp();
+        const int m1 = k + 1 - R;
+        const int n0 = (int)(issued - it.base);
+        const int cnt = min(m1 + kSlots + 1, it.nrows) - n0;
+        if (m1 >= 0 && cnt > 0) {
+            issue_rows(ring, it, n0, cnt, lane);
+            issued += cnt;
+        }
+    }
+    if (k < it.nrows) {
+        if (!__all_sync(kFull, row_landed(ring, it, k))) return false;
+        Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
+        ++k;
+    }
+    return true;
+}
+
+template <int R, bool FORCE, bool NARROW>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kMinBlocks) fd_batch_kernel(Args a) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -250,13 +374,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kMinBlocks) fd_batch_kern
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= *a.nitems) break;
-        const int s = a.item_slot[item];
-        const Lat& L = a.lats[s];
+        if (item >= a.counts[NARROW ? 1 : 0]) break;
+        const int2 e = a.items[(NARROW ? a.counts[0] : 0) + item];
+        const Lat& L = a.lats[e.x];
         if (a.step >= L.stop) continue;
         Item it;
-        const int local = item - L.item_begin;
-        const int strip = local % L.nstrips, seg = local / L.nstrips;
+        const int strip = e.y % L.nstrips, seg = e.y / L.nstrips;
         it.nx = L.nx;
         it.ny = L.ny;
         it.pitch = L.pitch;
@@ -270,47 +393,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kMinBlocks) fd_batch_kern
         it.ye = min(L.ny, it.yb + L.seg_rows);
         it.row_first = it.yb - 1 - R;
         it.nrows = it.ye - it.yb + 2 + 2 * R;
-        it.lane_stores = lane >= 1 && lane <= 30 && (it.strip0 - 4 + 4 * lane) < L.nx;
+        it.cols = NARROW ? kNarrowCols : kLoadCols;
+        it.lane_stores = NARROW
+            ? lane >= 2 && lane <= 29 && (it.strip0 - 4 + 2 * lane) < L.nx
+            : lane >= 1 && lane <= 30 && (it.strip0 - 4 + 4 * lane) < L.nx;
         it.base = base;
         const StreamCoeffs kc = L.k;
         __syncwarp();
         for (int k0 = 0; k0 < kSlots && k0 < it.nrows; k0 += 2)
             issue_rows(ring, it, k0, min(2, it.nrows - k0), lane);
         issued = base + min(kSlots, it.nrows);
-        Win w0 = {}, w1 = {}, w2 = {}, w3 = {};
-        Acc acc = {};
         int k = 0;
-        using Step = BatchRowStep<R, FORCE>;
-        for (; k + 1 < it.nrows; k += 2) {
-            const bool l0 = row_landed(ring, it, k), l1 = row_landed(ring, it, k + 1);
-            if (!__all_sync(kFull, l0 && l1)) {
-                ok = false;
-                break;
-            }
-            if (k >= warm_rows<R>()) {
-                Step::template run<false>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
-                Step::template run<false>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
-            } else {
-                Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
-                Step::template run<true>(ring, it, kc, lane, k + 1, w1, w0, w3, w2, acc);
-            }
-            __syncwarp();
-            const int m1 = k + 1 - R;
-            const int n0 = (int)(issued - base);
-            const int cnt = min(m1 + kSlots + 1, it.nrows) - n0;
-            if (m1 >= 0 && cnt > 0) {
-                issue_rows(ring, it, n0, cnt, lane);
-                issued += cnt;
-            }
-        }
-        if (ok && k < it.nrows) {
-            if (__all_sync(kFull, row_landed(ring, it, k))) {
-                Step::template run<true>(ring, it, kc, lane, k, w0, w1, w2, w3, acc);
-                ++k;
-            } else {
-                ok = false;
-            }
-        }
+        ok = item_rows<R, FORCE, NARROW>(ring, it, kc, lane, issued, k);
         consumed = base + k;
         base += it.nrows;
     }
@@ -456,13 +550,15 @@ struct fdlbm_batch_s {
     int max_items;
     std::vector<SlotHost> slots;
     std::vector<std::pair<long long, long long>> free_list;  // (offset, elems), sorted
-    std::vector<int> item_slot;
+    std::vector<int2> items;  // the wide list, then the narrow one
     bool items_dirty = true;
-    int nitems = 0;
+    int nitems = 0;      // both lists
+    int nnarrow = 0;     // items of the narrow list
     int seg_rows = 64;   // rows per work item (autotuned)
+    int narrow = 1;      // last strips of <= 56 columns on 2-column lanes (autotuned)
     int grid = 0;        // persistent CTAs
     // captured runs: graph per (steps, force)
-    cudaGraphExec_t exec[2][kMaxRun + 1];
+    cudaGraphExec_t exec[2][2][kMaxRun + 1];  // [force][narrow list non-empty][steps]
     int64_t launches = 0;
     char err[512];
 };
@@ -495,10 +591,10 @@ static bool batch_layout(const fdlbm_batch_params* bp, size_t* offs, size_t* tot
     o += al256((size_t)*arena_elems * 4);
     offs[1] = o;  // descriptors
     o += al256(sizeof(Lat) * bp->max_lattices);
-    offs[2] = o;  // items
-    o += al256(sizeof(int) * items);
-    offs[3] = o;  // counters of the steps of a run, then the item count
-    o += al256(sizeof(int) * (kMaxRun + 1));
+    offs[2] = o;  // items: (slot, index) pairs, the wide list then the narrow one
+    o += al256(sizeof(int2) * items);
+    offs[3] = o;  // counters of the steps of a run (wide, then narrow), then the two counts
+    o += al256(sizeof(int) * (2 * kMaxRun + 2));
     offs[4] = o;  // status
     o += 256;
     offs[5] = o;  // staging: 3 fields of the largest slot
@@ -524,24 +620,36 @@ static void fill_coeffs(const fdlbm_params& p, int R, StreamCoeffs* k) {
 }
 
 static int rebuild_items(fdlbm_batch_t* b) {
-    b->item_slot.clear();
+    b->items.clear();
+    std::vector<int2> narrow;
     for (size_t s = 0; s < b->slots.size(); ++s) {
         SlotHost& sl = b->slots[s];
         if (!sl.used) continue;
         sl.seg_rows = std::min(b->seg_rows, sl.p.ny);
         sl.nsegs = (sl.p.ny + sl.seg_rows - 1) / sl.seg_rows;
         sl.nstrips = (sl.p.nx + kStrip - 1) / kStrip;
-        for (int i = 0; i < sl.nstrips * sl.nsegs; ++i) b->item_slot.push_back((int)s);
+        const bool nar = b->narrow && sl.p.nx - (sl.nstrips - 1) * kStrip <= kNarrowStrip;
+        for (int i = 0; i < sl.nstrips * sl.nsegs; ++i) {
+            const int2 e = make_int2((int)s, i);
+            if (nar && i % sl.nstrips == sl.nstrips - 1)
+                narrow.push_back(e);
+            else
+                b->items.push_back(e);
+        }
     }
-    if ((int)b->item_slot.size() > b->max_items) return berr(b, FDLBM_ERR_NOMEM, "too many work items");
-    b->nitems = (int)b->item_slot.size();
+    const int nwide = (int)b->items.size();
+    b->items.insert(b->items.end(), narrow.begin(), narrow.end());
+    if ((int)b->items.size() > b->max_items) return berr(b, FDLBM_ERR_NOMEM, "too many work items");
+    b->nitems = (int)b->items.size();
+    b->nnarrow = (int)narrow.size();
+    const int counts[2] = {nwide, b->nnarrow};
     cudaError_t e = cudaSuccess;
     if (b->nitems)
-        e = cudaMemcpyAsync(b->ws + b->off_items, b->item_slot.data(), sizeof(int) * b->nitems,
+        e = cudaMemcpyAsync(b->ws + b->off_items, b->items.data(), sizeof(int2) * b->nitems,
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + b->off_counters + sizeof(int) * kMaxRun, &b->nitems,
-                            sizeof(int), cudaMemcpyHostToDevice, b->stream);
+        e = cudaMemcpyAsync(b->ws + b->off_counters + sizeof(int) * 2 * kMaxRun, counts,
+                            sizeof(counts), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "item upload");
     b->items_dirty = false;
@@ -552,7 +660,6 @@ static int rebuild_items(fdlbm_batch_t* b) {
 static int upload_lats(fdlbm_batch_t* b, const int* stop) {
     const int R = b->bp.scheme == FDLBM_SCHEME_FD3 ? 1 : 2;
     std::vector<Lat> L(b->slots.size());
-    int begin = 0;
     for (size_t s = 0; s < b->slots.size(); ++s) {
         const SlotHost& sl = b->slots[s];
         Lat& d = L[s];
@@ -567,8 +674,6 @@ static int upload_lats(fdlbm_batch_t* b, const int* stop) {
         d.nstrips = sl.nstrips;
         d.seg_rows = sl.seg_rows;
         d.nsegs = sl.nsegs;
-        d.item_begin = begin;
-        begin += sl.nstrips * sl.nsegs;
         d.stop = stop ? stop[s] : 0;
         d.cur = sl.cur;
         d.xi = (float)sl.p.wall_xi;
@@ -583,36 +688,51 @@ static int upload_lats(fdlbm_batch_t* b, const int* stop) {
     return FDLBM_OK;
 }
 
+// One step: the wide items' kernel, then (if the run carries narrow items)
+// the narrow items' kernel, each with its own work counter.
 template <int R, bool FORCE>
-static cudaError_t launch_batch_step(fdlbm_batch_t* b, int step) {
+static cudaError_t launch_batch_step(fdlbm_batch_t* b, int step, bool narrow) {
     const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(float) + kSlots * 8);
     Args a;
     a.arena = reinterpret_cast<float*>(b->ws + b->off_arena);
     a.lats = reinterpret_cast<const Lat*>(b->ws + b->off_lats);
-    a.item_slot = reinterpret_cast<const int*>(b->ws + b->off_items);
-    a.nitems = reinterpret_cast<const int*>(b->ws + b->off_counters) + kMaxRun;
+    a.items = reinterpret_cast<const int2*>(b->ws + b->off_items);
+    a.counts = reinterpret_cast<const int*>(b->ws + b->off_counters) + 2 * kMaxRun;
     a.step = step;
     a.counter = reinterpret_cast<int*>(b->ws + b->off_counters) + step;
     a.status = reinterpret_cast<int*>(b->ws + b->off_status);
-    fd_batch_kernel<R, FORCE><<<b->grid, kWarpsPerBlock * 32, smem, b->stream>>>(a);
+    fd_batch_kernel<R, FORCE, false><<<b->grid, kWarpsPerBlock * 32, smem, b->stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !narrow) return e;
+    a.counter = reinterpret_cast<int*>(b->ws + b->off_counters) + kMaxRun + step;
+    fd_batch_kernel<R, FORCE, true><<<b->grid, kWarpsPerBlock * 32, smem, b->stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int R, bool FORCE, bool NARROW>
+static cudaError_t prepare_one(fdlbm_batch_t* b, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(fd_batch_kernel<R, FORCE, NARROW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fd_batch_kernel<R, FORCE, NARROW>,
+                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 template <int R, bool FORCE>
 static cudaError_t prepare_kernel(fdlbm_batch_t* b) {
     const size_t smem = kWarpsPerBlock * (kSlots * 3 * kLoadCols * sizeof(float) + kSlots * 8);
-    cudaError_t e = cudaFuncSetAttribute(fd_batch_kernel<R, FORCE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fd_batch_kernel<R, FORCE>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = prepare_one<R, FORCE, false>(b, smem);
+    if (e == cudaSuccess) e = prepare_one<R, FORCE, true>(b, smem);
     if (e != cudaSuccess) return e;
     if (b->grid == 0) {
-        int sms = 0, per_sm = 0;
+        int sms = 0, per_sm = 0, per_sm_narrow = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fd_batch_kernel<R, FORCE>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fd_batch_kernel<R, FORCE, false>,
                                                       kWarpsPerBlock * 32, smem);
-        b->grid = std::max(1, sms * per_sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_narrow,
+                                                      fd_batch_kernel<R, FORCE, true>,
+                                                      kWarpsPerBlock * 32, smem);
+        b->grid = std::max(1, sms * std::min(per_sm, per_sm_narrow));
     }
     return cudaSuccess;
 }
@@ -624,7 +744,8 @@ static int run_steps(fdlbm_batch_t* b, int steps, bool force) {
     cudaError_t e = (R == 1) ? (force ? prepare_kernel<1, true>(b) : prepare_kernel<1, false>(b))
                              : (force ? prepare_kernel<2, true>(b) : prepare_kernel<2, false>(b));
     if (e != cudaSuccess) return bcuda(b, e, "kernel attributes");
-    cudaGraphExec_t& ex = b->exec[force ? 1 : 0][steps];
+    const bool narrow = b->nnarrow > 0;
+    cudaGraphExec_t& ex = b->exec[force ? 1 : 0][narrow ? 1 : 0][steps];
     if (!ex) {
         cudaStream_t cap;
         e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
@@ -633,10 +754,12 @@ static int run_steps(fdlbm_batch_t* b, int steps, bool force) {
         b->stream = cap;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(b->ws + b->off_counters, 0, sizeof(int) * steps, cap);
+            e = cudaMemsetAsync(b->ws + b->off_counters, 0, sizeof(int) * 2 * kMaxRun, cap);
         for (int s = 0; s < steps && e == cudaSuccess; ++s)
-            e = (R == 1) ? (force ? launch_batch_step<1, true>(b, s) : launch_batch_step<1, false>(b, s))
-                         : (force ? launch_batch_step<2, true>(b, s) : launch_batch_step<2, false>(b, s));
+            e = (R == 1) ? (force ? launch_batch_step<1, true>(b, s, narrow)
+                                  : launch_batch_step<1, false>(b, s, narrow))
+                         : (force ? launch_batch_step<2, true>(b, s, narrow)
+                                  : launch_batch_step<2, false>(b, s, narrow));
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         b->stream = user;
@@ -651,7 +774,7 @@ static int run_steps(fdlbm_batch_t* b, int steps, bool force) {
     }
     e = cudaGraphLaunch(ex, b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "graph launch");
-    b->launches += steps;
+    b->launches += (int64_t)steps * (narrow ? 2 : 1);
     return FDLBM_OK;
 }
 
@@ -709,9 +832,10 @@ int fdlbm_batch_create(const fdlbm_batch_params* bp, void* workspace, size_t byt
 
 void fdlbm_batch_destroy(fdlbm_batch_t* b) {
     if (!b) return;
-    for (auto& row : b->exec)
-        for (auto& ex : row)
-            if (ex) cudaGraphExecDestroy(ex);
+    for (auto& by_force : b->exec)
+        for (auto& row : by_force)
+            for (auto& ex : row)
+                if (ex) cudaGraphExecDestroy(ex);
     delete b;
 }
 
@@ -928,16 +1052,26 @@ int fdlbm_batch_set_segment_rows(fdlbm_batch_t* b, int32_t rows) {
     return FDLBM_OK;
 }
 
+int fdlbm_batch_set_narrow_strips(fdlbm_batch_t* b, int32_t on) {
+    if (!b || (on != 0 && on != 1)) return FDLBM_ERR_INVALID;
+    if (on != b->narrow) {
+        b->narrow = on;
+        b->items_dirty = true;  // the two item lists are rebuilt by the next step
+    }
+    return FDLBM_OK;
+}
+
 int fdlbm_batch_set_grid(fdlbm_batch_t* b, int32_t ctas) {
     if (!b || ctas < 0) return FDLBM_ERR_INVALID;
     if (ctas != b->grid) {
         b->grid = ctas;  // 0: back to one wave of resident CTAs
-        for (auto& row : b->exec)
-            for (auto& ex : row)
-                if (ex) {
-                    cudaGraphExecDestroy(ex);
-                    ex = nullptr;
-                }
+        for (auto& by_force : b->exec)
+            for (auto& row : by_force)
+                for (auto& ex : row)
+                    if (ex) {
+                        cudaGraphExecDestroy(ex);
+                        ex = nullptr;
+                    }
     }
     return FDLBM_OK;
 }

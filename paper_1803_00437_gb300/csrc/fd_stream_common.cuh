@@ -473,5 +473,138 @@ __device__ __forceinline__ void stream_row(const float2 nr[2], const float2 nux[
     if (R == 2) dm3 = d1new;
 }
 
+// ---- narrow strips: one column pair per lane ------------------------------------
+// The same step on lanes that hold 2 consecutive columns (a warp covers 64
+// columns; with two halo lanes on each side, 56 output columns): used for
+// the last, partial strip of a lattice, where 4-column lanes would compute
+// up to 128 columns for a few stored ones.  Lane L holds columns 2L - 4 and
+// 2L - 3 of its strip; lanes 0 and 31 hold only the stencil's outer columns,
+// lanes 1 and 30 rebuild the populations that enter the strip.
+
+struct Win1 {
+    float2 v[W_N];
+};
+struct Acc1 {
+    float2 ar, ax, ay, us, ud;
+};
+
+// x-derivative (scaled by 2 or 8) at the lane's 2 columns.
+template <int R>
+__device__ __forceinline__ float2 deriv_x1(float2 v) {
+    const float l1 = __shfl_up_sync(kFull, v.y, 1);
+    const float r0 = __shfl_down_sync(kFull, v.x, 1);
+    const float2 d1 = make_float2(v.y - l1, r0 - v.x);  // f(+1) - f(-1)
+    if (R == 1) return d1;
+    // 8 d/dx = 6 (f(+1) - f(-1)) - (f(+2) - f(-2)): columns +-2 are the
+    // neighbouring lanes' pairs
+    const float l0 = __shfl_up_sync(kFull, v.x, 1);
+    const float r1 = __shfl_down_sync(kFull, v.y, 1);
+    return fma2(sp(6.f), d1, sub2(make_float2(l0, l1), make_float2(r0, r1)));
+}
+
+template <int R>
+__device__ __forceinline__ void window_row1(float2 nr, float2 nux, float2 nuy, float2 cdr,
+                                            float2 cux, float2 cuy, Win1& fm2, Win1& dm3) {
+    const float2 jx = fma2(nr, nux, nux), jy = fma2(nr, nuy, nuy);
+    const float2 pxy = mul2(jx, nuy), pyy = mul2(jy, nuy);
+    if (R == 1) {
+        fm2.v[W_R] = nr;
+        fm2.v[W_JX] = jx;
+        fm2.v[W_JY] = jy;
+        fm2.v[W_PXY] = pxy;
+        fm2.v[W_PYY] = pyy;
+    } else {
+        const float2 cjx = fma2(cdr, cux, cux), cjy = fma2(cdr, cuy, cuy);
+        dm3.v[W_R] = sub2(cdr, nr);
+        dm3.v[W_JX] = sub2(cjx, jx);
+        dm3.v[W_JY] = sub2(cjy, jy);
+        dm3.v[W_PXY] = sub2(mul2(cjx, cuy), pxy);
+        dm3.v[W_PYY] = sub2(mul2(cjy, cuy), pyy);
+    }
+}
+
+// One row of a narrow strip; the single-pair form of stream_row (finite
+// differences only, R = 1 or 2).
+template <int R, bool FORCE>
+__device__ __forceinline__ void stream_row1(float2 nr, float2 nux, float2 nuy, float2 cdr,
+                                            float2 cux, float2 cuy, const StreamCoeffs& k,
+                                            Win1& fm2, Win1& fm1, Win1& dm3, Win1& dm2,
+                                            Acc1& acc, float2& odr, float2& oux, float2& ouy) {
+    static_assert(R == 1 || R == 2, "narrow strips carry the finite-difference steps");
+    Win1 nw;
+    {
+        const float2 jx = fma2(nr, nux, nux), jy = fma2(nr, nuy, nuy);
+        nw.v[W_R] = nr;
+        nw.v[W_JX] = jx;
+        nw.v[W_JY] = jy;
+        nw.v[W_PXY] = mul2(jx, nuy);
+        nw.v[W_PYY] = mul2(jy, nuy);
+    }
+    Win1 rebuilt;
+    if (R == 2) {
+        const float2 jx = fma2(cdr, cux, cux), jy = fma2(cdr, cuy, cuy);
+        rebuilt.v[W_R] = cdr;
+        rebuilt.v[W_JX] = jx;
+        rebuilt.v[W_JY] = jy;
+        rebuilt.v[W_PXY] = mul2(jx, cuy);
+        rebuilt.v[W_PYY] = mul2(jy, cuy);
+    }
+    const Win1& cen = (R == 1) ? fm1 : rebuilt;
+    Win1 dy, d1new;
+#pragma unroll
+    for (int f = 0; f < W_N; ++f) {
+        if (R == 1) {
+            dy.v[f] = sub2(nw.v[f], fm2.v[f]);
+        } else {
+            d1new.v[f] = sub2(cen.v[f], nw.v[f]);
+            dy.v[f] = add2(fma2(sp(-6.f), dm2.v[f], dm3.v[f]), d1new.v[f]);
+        }
+    }
+    const float2 pxx = mul2(cen.v[W_JX], cux);
+    const float2 dxr = deriv_x1<R>(cen.v[W_R]), dxjx = deriv_x1<R>(cen.v[W_JX]);
+    const float2 dxjy = deriv_x1<R>(cen.v[W_JY]), dxpxx = deriv_x1<R>(pxx);
+    const float2 dxpxy = deriv_x1<R>(cen.v[W_PXY]);
+    float2 g[9];
+    reconstruct2<FORCE>(cen.v[W_R], cux, cuy, cen.v[W_JX], cen.v[W_JY], pxx, cen.v[W_PXY],
+                        cen.v[W_PYY], dxr, dy.v[W_R], dxjx, dy.v[W_JX], dxjy, dy.v[W_JY],
+                        dxpxx, dxpxy, dy.v[W_PXY], dy.v[W_PYY], k, g);
+    // right-going (1, 5, 8) of column 1 to the next lane, left-going
+    // (3, 6, 7) of column 0 back
+    const float in1 = __shfl_up_sync(kFull, g[1].y, 1);
+    const float in5 = __shfl_up_sync(kFull, g[5].y, 1);
+    const float in8 = __shfl_up_sync(kFull, g[8].y, 1);
+    const float in3 = __shfl_down_sync(kFull, g[3].x, 1);
+    const float in6 = __shfl_down_sync(kFull, g[6].x, 1);
+    const float in7 = __shfl_down_sync(kFull, g[7].x, 1);
+    // column 0 takes 1, 5, 8 from the left lane and 3, 6, 7 from column 1;
+    // column 1 takes 1, 5, 8 from column 0 and 3, 6, 7 from the right lane
+    const float2 ss = make_float2(g[0].x + (in1 + g[3].y), g[0].y + (g[1].x + in3));
+    const float2 ds = make_float2(in1 - g[3].y, g[1].x - in3);
+    const float2 su = make_float2(g[2].x + (in5 + g[6].y), g[2].y + (g[5].x + in6));
+    const float2 du = make_float2(in5 - g[6].y, g[5].x - in6);
+    const float2 sd = make_float2(g[4].x + (g[7].y + in8), g[4].y + (in7 + g[8].x));
+    const float2 dd = make_float2(in8 - g[7].y, g[8].x - in7);
+    // close row c - 1: u = J - J dr / (1 + dr)
+    const float2 drn = add2(acc.ar, sd);
+    float2 px = add2(acc.ax, dd);
+    float2 py = sub2(acc.ay, sd);
+    if (FORCE) {
+        px = add2(px, sp(k.hfx));
+        py = add2(py, sp(k.hfy));
+    }
+    const float2 nrho = fma2(drn, sp(-1.f), sp(-1.f));  // -(1 + dr)
+    const float2 ninv = make_float2(rcp_approx(nrho.x), rcp_approx(nrho.y));
+    odr = drn;
+    oux = fma2(mul2(px, drn), ninv, px);
+    ouy = fma2(mul2(py, drn), ninv, py);
+    acc.ar = add2(acc.us, ss);
+    acc.ax = add2(acc.ud, ds);
+    acc.ay = acc.us;
+    acc.us = su;
+    acc.ud = du;
+    if (R == 1) fm2 = nw;
+    if (R == 2) dm3 = d1new;
+}
+
 }  // namespace stream
 }  // namespace fdlbm

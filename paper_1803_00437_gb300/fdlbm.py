@@ -113,6 +113,7 @@ def load_library(path: str | None = None):
         L.fdlbm_batch_sync.argtypes = [vp]
         L.fdlbm_batch_set_segment_rows.argtypes = [vp, i32]
         L.fdlbm_batch_set_grid.argtypes = [vp, i32]
+        L.fdlbm_batch_set_narrow_strips.argtypes = [vp, i32]
         L.fdlbm_batch_last_error.argtypes = [vp]
         L.fdlbm_batch_last_error.restype = cp
         L.fdlbm_batch_launch_count.argtypes = [vp]
@@ -122,7 +123,8 @@ def load_library(path: str | None = None):
         for name in ("fdlbm_batch_create", "fdlbm_batch_add", "fdlbm_batch_remove",
                      "fdlbm_batch_init", "fdlbm_batch_init_modes", "fdlbm_batch_step",
                      "fdlbm_batch_moments", "fdlbm_batch_reduce", "fdlbm_batch_sync",
-                     "fdlbm_batch_set_segment_rows", "fdlbm_batch_set_grid"):
+                     "fdlbm_batch_set_segment_rows", "fdlbm_batch_set_grid",
+                     "fdlbm_batch_set_narrow_strips"):
             getattr(L, name).restype = ctypes.c_int
         L.fdlbm_get_populations.argtypes = [vp, fp]
         L.fdlbm_get_populations.restype = ctypes.c_int
@@ -419,7 +421,8 @@ class Batch:
     size 16..max_side, periodic or walls in y, each with its own rates and
     force.  The workspace (arena + tables) is a torch uint8 CUDA tensor."""
 
-    # segment lengths measured best per (device, scheme, size class); filled by tune()
+    # (segment length, narrow last strips) measured best per (device, scheme,
+    # size class), with every candidate's time; filled by tune()
     _tuned: dict = {}
 
     def __init__(self, scheme="fd5", max_lattices=64, arena_bytes=1 << 30, max_side=512,
@@ -517,6 +520,9 @@ class Batch:
     def set_grid(self, ctas: int):
         self._check(self.lib.fdlbm_batch_set_grid(self._h, int(ctas)), "grid")
 
+    def set_narrow_strips(self, on: bool):
+        self._check(self.lib.fdlbm_batch_set_narrow_strips(self._h, int(bool(on))), "strips")
+
     @property
     def count(self) -> int:
         return int(self.lib.fdlbm_batch_count(self._h))
@@ -529,31 +535,47 @@ class Batch:
         sides = [max(c.nx, c.ny) for c in self.configs.values()] or [0]
         return int(2 ** round(np.log2(max(16, float(np.mean(sides))))))
 
-    def tune(self, steps: int = 8, candidates=(16, 32, 64, 128, 256)) -> int:
-        """Autotuner: time `steps` steps of the current slots for each row-segment
-        length and keep the fastest (cached per device, scheme and size class).
-        The slots' states advance while tuning: call it before initialising
-        them, or re-initialise afterwards."""
+    def tune(self, steps: int = 8, candidates=(16, 32, 64, 128, 256), strips=(True, False)) -> int:
+        """Autotuner over the tile shape: times `steps` steps of the current
+        slots for each row-segment length and each form of the lattices' last
+        strips (2-column lanes for a last strip of <= 56 columns, or 4-column
+        lanes throughout), keeps the fastest pair (cached per device, scheme
+        and size class) and returns its segment length.  The slots' states
+        advance while tuning: call it before initialising them, or
+        re-initialise afterwards."""
         import torch
         key = (torch.cuda.get_device_name(self.device), self.scheme, self._size_class())
         if key in Batch._tuned:
-            self.set_segment_rows(Batch._tuned[key][0])
-            return Batch._tuned[key][0]
-        timings = {}
-        for rows in candidates:
+            rows, narrow = Batch._tuned[key][0]
             self.set_segment_rows(rows)
-            self.step(1)  # work list and graph for this choice
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(self.stream)
-            self.step(steps)
-            e1.record(self.stream)
-            self.sync()
-            timings[rows] = e0.elapsed_time(e1) / steps
+            self.set_narrow_strips(narrow)
+            return rows
+        timings = {}
+        for narrow in strips:
+            self.set_narrow_strips(narrow)
+            for rows in candidates:
+                self.set_segment_rows(rows)
+                self.step(1)  # work list and graph for this choice
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                self.step(steps)
+                e1.record(self.stream)
+                self.sync()
+                timings[(rows, narrow)] = e0.elapsed_time(e1) / steps
         best = min(timings, key=timings.get)
         Batch._tuned[key] = (best, timings)
-        self.set_segment_rows(best)
-        return best
+        self.set_segment_rows(best[0])
+        self.set_narrow_strips(best[1])
+        return best[0]
+
+    @property
+    def tuned(self):
+        """The autotuner's choice for this batch's size class, (rows, narrow
+        strips), or None before tune()."""
+        import torch
+        key = (torch.cuda.get_device_name(self.device), self.scheme, self._size_class())
+        return Batch._tuned.get(key, (None,))[0]
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -61,6 +61,8 @@ def test_status_strings_and_null_handles(lib):
     assert F.status_string(-5) == "FDLBM_ERR_DIVERGED"
     assert lib.fdlbm_step(None, 1) == F.ERR_INVALID
     assert lib.fdlbm_launch_count(None) == -1
+    assert lib.fdlbm_batch_set_narrow_strips(None, 1) == F.ERR_INVALID
+    assert lib.fdlbm_batch_set_segment_rows(None, 64) == F.ERR_INVALID
     assert lib.fdlbm_create(None, None, 0, None, None) == F.ERR_INVALID
     out = ctypes.c_void_p()
     p = F.LatticeConfig(8, 8).params()

@@ -55,6 +55,38 @@ def test_batch_equals_single_lattices(scheme):
         assert max_err(got, single, amplitude(f)) <= TOL32, (cfg.nx, cfg.ny)
 
 
+@pytest.mark.parametrize("scheme", ["fd3", "fd5"])
+def test_narrow_last_strips_equal_wide_ones(scheme):
+    """A lattice's last strip of <= 56 columns on 2-column lanes gives the same
+    lattice bit for bit as 4-column lanes (the same operations per column):
+    single narrow strips (16, 40, 56 columns), a narrow last strip after full
+    ones (128, 176, 385), one just too wide (57, 300), periodic and channels
+    with force."""
+    from paper_1803_00437_gb300 import fdlbm as F
+    shapes = [(16, 20), (40, 33), (56, 24), (57, 31), (128, 40), (176, 45), (300, 17), (385, 26)]
+    out = {}
+    for narrow in (True, False):
+        b = F.Batch(scheme, max_lattices=2 * len(shapes), arena_bytes=64 << 20, max_side=512)
+        b.set_narrow_strips(narrow)
+        slots = []
+        for i, (nx, ny) in enumerate(shapes):
+            for walls in (False, True):
+                kw = dict(boundary="walls_y", wall_xi=0.4, force=(1e-5, 0.0)) if walls else {}
+                cfg = F.LatticeConfig(nx, ny, scheme, s_xx=F.nu_to_s(0.01 + 0.005 * i), s_e=1.5,
+                                      **kw)
+                s = b.add(cfg)
+                b.init(s, *_to_dev(_fields(nx, ny, 300 + i)))
+                slots.append(s)
+        b.step(23)
+        b.sync()
+        out[narrow] = [[t.cpu().numpy() for t in b.moments(s)] for s in slots]
+        b.sync()
+        b.close()
+    for a, w in zip(out[True], out[False]):
+        for x, y in zip(a, w):
+            assert np.array_equal(x, y)
+
+
 def test_batch_against_oracle(oracle):
     from paper_1803_00437_gb300 import fdlbm as F
     b = F.Batch("fd5", max_lattices=4, arena_bytes=16 << 20, max_side=256)
