@@ -213,9 +213,10 @@ int fdlbm_reduce(fdlbm_t* h, int32_t what, const double* args, double* out);
  *
  * Many independent lattices (periodic, or channels with walls in y) of any
  * size (16 <= nx, ny <= max_side), each with its own relaxation rates and
- * force, stepped together by one persistent FD-LBM kernel per step (the
- * scheme of Sec. 2 with the streaming data path); runs of up to 64 steps are
- * captured once in a CUDA graph and replayed.  FP32 storage.  Slots are
+ * force, stepped together by persistent FD-LBM kernels (the scheme of Sec. 2
+ * with the streaming data path; a second kernel per step takes the lattices'
+ * narrow last strips, see fdlbm_batch_set_narrow_strips); runs of up to 64
+ * steps are captured once in a CUDA graph and replayed.  FP32 storage.  Slots are
  * added and removed between calls (continuous batching); each slot's state
  * lives in a caller-owned arena with 8 periodic ghost columns per row side.
  * Results equal those of a single-lattice handle with the same parameters
