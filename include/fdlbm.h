@@ -267,10 +267,11 @@ int fdlbm_batch_reduce(fdlbm_batch_t* b, int32_t slot, int32_t what, const doubl
 int fdlbm_batch_sync(fdlbm_batch_t* b);
 /* Tuning knobs (chosen by the autotuner in the Python layer): rows per work
  * item (>= 8), persistent CTAs (0 = one wave of resident CTAs), and the strip
- * form of each lattice's last strip: with narrow strips on (1, the default)
- * a last strip of at most 56 columns runs on lanes of 2 columns (a warp
- * covers 56 output columns) instead of 4 (120), so that fewer columns are
- * computed for the ones stored; off (0): every strip on 4-column lanes.
+ * form of each lattice's last strip: with narrow strips on (1) a last strip
+ * of at most 56 columns runs on lanes of 2 columns (a warp covers 56 output
+ * columns) instead of 4 (120), in a second kernel per step, so that fewer
+ * columns are computed for the ones stored; off (0, the default): every strip
+ * on 4-column lanes, one kernel per step.
  * Both forms compute the same populations in the same order (Sec. 2, Eq. 2).
  * Settings apply from the next fdlbm_batch_step.  FDLBM_ERR_INVALID for a
  * NULL handle or an out-of-range value. */

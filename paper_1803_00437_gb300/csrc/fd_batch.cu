@@ -555,7 +555,7 @@ struct fdlbm_batch_s {
     int nitems = 0;      // both lists
     int nnarrow = 0;     // items of the narrow list
     int seg_rows = 64;   // rows per work item (autotuned)
-    int narrow = 1;      // last strips of <= 56 columns on 2-column lanes (autotuned)
+    int narrow = 0;      // last strips of <= 56 columns on 2-column lanes (autotuned)
     int grid = 0;        // persistent CTAs
     // captured runs: graph per (steps, force)
     cudaGraphExec_t exec[2][2][kMaxRun + 1];  // [force][narrow list non-empty][steps]
