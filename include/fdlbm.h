@@ -184,6 +184,19 @@ int fdlbm_init_modes(fdlbm_t* h, int32_t n_modes, const double* modes, double me
 /* Advance nsteps >= 0 time steps (asynchronous).  nsteps = 0 is a no-op. */
 int fdlbm_step(fdlbm_t* h, int64_t nsteps);
 
+/* The launch plan of the streaming step (the time step of Sec. 2, and
+ * LW-ACM's of Sec. 1-b) for an nx x ny lattice when resident_ctas CTAs of it
+ * fit on the device at once (fdlbm_step queries that occupancy itself).  The
+ * rows are cut into segments of equal length, chosen from a cost model of the
+ * rows a segment streams beyond its own and of the launch's tail; a CTA
+ * covers a 240-column strip of one segment.  scheme: FDLBM_SCHEME_FD3, _FD5
+ * or _LWACM; storage: FDLBM_STORAGE_*.  plan (host, 4 int32): rows per
+ * segment, segments, CTA strips, CTAs.  Host-only: needs no device.
+ * FDLBM_ERR_INVALID for a NULL plan, a size or resident_ctas below 1, or
+ * another scheme or storage. */
+int fdlbm_stream_plan(int32_t nx, int32_t ny, int32_t scheme, int32_t storage,
+                      int32_t resident_ctas, int32_t* plan);
+
 /* Write the current drho, ux, uy into device arrays (nx*ny floats each). */
 int fdlbm_moments(fdlbm_t* h, float* drho, float* ux, float* uy);
 

@@ -549,3 +549,30 @@ cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst) {
 }
 
 }  // namespace fdlbm
+
+extern "C" int fdlbm_stream_plan(int32_t nx, int32_t ny, int32_t scheme, int32_t storage,
+                                 int32_t resident_ctas, int32_t* plan) {
+    using namespace fdlbm;
+    if (!plan || nx < 1 || ny < 1 || resident_ctas < 1) return FDLBM_ERR_INVALID;
+    int R;
+    switch (scheme) {
+        case FDLBM_SCHEME_FD3: R = 1; break;
+        case FDLBM_SCHEME_FD5: R = 2; break;
+        case FDLBM_SCHEME_LWACM: R = 0; break;
+        default: return FDLBM_ERR_INVALID;
+    }
+    int elem;
+    switch (storage) {
+        case FDLBM_STORAGE_F32: elem = 4; break;
+        case FDLBM_STORAGE_F16:
+        case FDLBM_STORAGE_BF16:
+        case FDLBM_STORAGE_I16: elem = 2; break;
+        default: return FDLBM_ERR_INVALID;
+    }
+    const Plan p = make_plan(nx, ny, R, kWarps, resident_ctas, elem);
+    plan[0] = p.seg_rows;
+    plan[1] = p.nsegs;
+    plan[2] = p.ncstrips;
+    plan[3] = p.nitems;
+    return FDLBM_OK;
+}

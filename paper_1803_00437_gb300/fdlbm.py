@@ -114,6 +114,8 @@ def load_library(path: str | None = None):
         L.fdlbm_batch_set_segment_rows.argtypes = [vp, i32]
         L.fdlbm_batch_set_grid.argtypes = [vp, i32]
         L.fdlbm_batch_set_narrow_strips.argtypes = [vp, i32]
+        L.fdlbm_stream_plan.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32)]
+        L.fdlbm_stream_plan.restype = ctypes.c_int
         L.fdlbm_batch_last_error.argtypes = [vp]
         L.fdlbm_batch_last_error.restype = cp
         L.fdlbm_batch_launch_count.argtypes = [vp]
@@ -148,6 +150,19 @@ def load_library(path: str | None = None):
 
 def status_string(status: int) -> str:
     return load_library().fdlbm_status_string(int(status)).decode()
+
+
+def stream_plan(nx: int, ny: int, scheme: str = "fd5", storage: str = "f32",
+                resident_ctas: int = 152 * 8) -> dict:
+    """The streaming step's launch plan (fdlbm_stream_plan): rows per segment,
+    segments, CTA strips and CTAs for an nx x ny lattice; host-only."""
+    lib = load_library()
+    out = (ctypes.c_int32 * 4)()
+    rc = lib.fdlbm_stream_plan(int(nx), int(ny), SCHEMES[scheme], STORAGES[storage],
+                               int(resident_ctas), out)
+    if rc != OK:
+        raise FdlbmError(rc, f"stream plan: {status_string(rc)}")
+    return {"seg_rows": out[0], "nsegs": out[1], "strips": out[2], "ctas": out[3]}
 
 
 def nu_to_s(nu: float) -> float:
