@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--side", type=int, default=N_SIDE, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the cost model's row segments for the streaming steps")
     ap.add_argument("--workload", choices=["throughput", "batched", "serving"],
                     default="throughput",
                     help="throughput: the 8192^2 headline line (default); batched: 4096 "
@@ -326,6 +328,14 @@ def run_ours(args):
         lat = F.Lattice(cfg, device=dev, stream=stream)
         lat.init_modes(modes)
         lats[scheme] = lat
+    # set-up, untimed: the streaming steps' row segments are chosen by timing
+    # the library's candidate plans on this device (the state is restored)
+    plans = {}
+    if not args.no_tune:
+        for scheme in ("fd5", "lwacm"):
+            tuned = lats[scheme].tune()
+            if tuned is not None:
+                plans[scheme] = lats[scheme].stream_plan()
     torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(local)
@@ -419,7 +429,12 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": side, "ny": side, "scheme": "fd5",
                    "l2": "state larger than L2 (805 MB FD-LBM and LW-ACM, 2.4 GB MRT): no flush",
-                   "parallelism": f"{world} independent lattice(s), one per GPU"},
+                   "parallelism": f"{world} independent lattice(s), one per GPU",
+                   "stream_plans": {k: {q: v[q] for q in ("seg_rows", "nsegs", "tail_rows",
+                                                          "ntail", "ctas")}
+                                    for k, v in plans.items()},
+                   "plan_choice": "tuned: fastest of the library's candidate plans"
+                                  if plans else "the library's cost model"},
         "roofline": roofline("fd5", "fd_step"),
         "mrt": {"value": round(mrt_value, 1), "unit": "MLUPS",
                 "ms_per_step": round(mrt_ms, 5), "roofline": roofline("mrt", "mrt_step")},

@@ -186,16 +186,51 @@ int fdlbm_step(fdlbm_t* h, int64_t nsteps);
 
 /* The launch plan of the streaming step (the time step of Sec. 2, and
  * LW-ACM's of Sec. 1-b) for an nx x ny lattice when resident_ctas CTAs of it
- * fit on the device at once (fdlbm_step queries that occupancy itself).  The
- * rows are cut into segments of equal length, chosen from a cost model of the
- * rows a segment streams beyond its own and of the launch's tail; a CTA
- * covers a 240-column strip of one segment.  scheme: FDLBM_SCHEME_FD3, _FD5
- * or _LWACM; storage: FDLBM_STORAGE_*.  plan (host, 4 int32): rows per
- * segment, segments, CTA strips, CTAs.  Host-only: needs no device.
+ * fit on the device at once (fdlbm_step queries that occupancy itself and
+ * computes the plan once per handle).  A CTA covers a 240-column strip of one
+ * row segment.  The rows are cut into a first part of long segments followed
+ * by short ones (the finite-difference steps, where this measured faster),
+ * or into segments of one length (LW-ACM, and wherever the cost model finds
+ * that cheaper); the model counts the rows a segment streams beyond its own,
+ * the launch's tail, and the spread of the long segments' finishing times
+ * that the short ones must absorb.  scheme: FDLBM_SCHEME_FD3, _FD5 or
+ * _LWACM; storage: FDLBM_STORAGE_*.  plan (host, 6 int32): rows per long
+ * segment, long segments, rows per short segment, short segments (0 when all
+ * are equal), CTA strips, CTAs.  Host-only: needs no device.
  * FDLBM_ERR_INVALID for a NULL plan, a size or resident_ctas below 1, or
  * another scheme or storage. */
 int fdlbm_stream_plan(int32_t nx, int32_t ny, int32_t scheme, int32_t storage,
                       int32_t resident_ctas, int32_t* plan);
+
+/* Candidate launch plans of the streaming step, for measuring which is
+ * fastest on the device at hand (the cost model ranks plans whose step times
+ * differ by a few per cent, below its accuracy).  Same arguments as
+ * fdlbm_stream_plan; out (host, 3 * max int32) receives per candidate the
+ * rows per long segment, the long segments, and the rows per short segment
+ * (equal to the first entry when all segments are equal), the model's plan
+ * first and the rest cheapest first by the model; *count the number written
+ * (1 <= *count <= max).  FDLBM_ERR_INVALID as for fdlbm_stream_plan, or for
+ * max < 1 or a NULL count. */
+int fdlbm_stream_plan_candidates(int32_t nx, int32_t ny, int32_t scheme, int32_t storage,
+                                 int32_t resident_ctas, int32_t* out, int32_t max,
+                                 int32_t* count);
+
+/* Use the given row segments for this lattice's streaming step instead of the
+ * model's plan: nsegs segments of seg_rows rows, then the remaining rows in
+ * segments of tail_rows rows (equal segments of seg_rows rows if nsegs *
+ * seg_rows >= ny).  (0, 0, 0) returns to the model's plan.  Any plan gives
+ * the same lattice bit for bit; only the step time changes.  FDLBM_ERR_INVALID
+ * for a value below 1 (other than all three 0), seg_rows > ny, or a lattice
+ * whose steps do not run on the streaming kernel (MRT, nine points, the tiled
+ * kernel). */
+int fdlbm_set_stream_plan(fdlbm_t* h, int32_t seg_rows, int32_t nsegs, int32_t tail_rows);
+
+/* The launch plan this lattice's streaming step uses: plan (host, 7 int32)
+ * receives the six entries of fdlbm_stream_plan, then the resident CTAs the
+ * device holds (the count the model's plan was computed for).  Known once the
+ * lattice has stepped: FDLBM_ERR_INVALID before its first step, for a NULL
+ * plan, or for a lattice whose steps do not run on the streaming kernel. */
+int fdlbm_get_stream_plan(fdlbm_t* h, int32_t* plan);
 
 /* Write the current drho, ux, uy into device arrays (nx*ny floats each). */
 int fdlbm_moments(fdlbm_t* h, float* drho, float* ux, float* uy);

@@ -27,6 +27,7 @@
 // exchanged by shuffles, summed per destination row and closed when the row
 // below has contributed.
 #include <algorithm>
+#include <vector>
 #include <type_traits>
 
 #include "fd_stream_common.cuh"
@@ -68,7 +69,9 @@ struct StreamArgs {
     float xi;         // wall offset (channels)
     int nstrips;      // warp strips of 120 columns
     int ncstrips;     // CTA strips (W warp strips each, the last maybe fewer)
-    int seg_rows, nsegs, nitems;
+    // rows [0, nsegs seg_rows) in segments of seg_rows rows, the rest of the
+    // rows in segments of tail_rows; items list the first kind, then the second
+    int seg_rows, nsegs, tail_rows, nitems;
     StreamCoeffs k;
     Quant q;          // fixed-point scale (FDLBM_STORAGE_I16)
     int* status;      // device status word (FDLBM_ERR_TIMEOUT on a lost copy)
@@ -87,11 +90,15 @@ struct Item {
 template <int R>
 __device__ __forceinline__ Item make_item(const StreamArgs& a, int item, int W) {
     Item it;
-    const int cs = item % a.ncstrips, seg = item / a.ncstrips;
+    const int nfirst = a.ncstrips * a.nsegs;
+    const bool first = item < nfirst;
+    const int i = first ? item : item - nfirst;
+    const int cs = i % a.ncstrips, seg = i / a.ncstrips;
+    const int rows = first ? a.seg_rows : a.tail_rows;
     it.strip0 = cs * W * kStrip;
     it.active = min(W, a.nstrips - cs * W);
-    it.yb = seg * a.seg_rows;
-    it.ye = min(a.ny, it.yb + a.seg_rows);
+    it.yb = (first ? 0 : a.nsegs * a.seg_rows) + seg * rows;
+    it.ye = min(a.ny, it.yb + rows);
     it.row_first = it.yb - 1 - R;
     it.nrows = it.ye - it.yb + 2 + 2 * R;
     it.x0 = wrap_index(it.strip0 - kHalo, a.nx);
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(W * 32, kWarpsPerSM / W) fd_step_stream_kernel
 }
 
 struct Plan {
-    int W, ncstrips, seg_rows, nsegs, nitems, blocks;
+    int W, ncstrips, seg_rows, nsegs, tail_rows, ntail, nitems, blocks;
 };
 
 // Warps per CTA.  Two warps share one ring: the row copies and the halo
@@ -421,45 +428,195 @@ struct Plan {
 // an mbarrier arrival with its pending count: all within 1 %).
 constexpr int kWarps = 2;
 
-// Row segments of equal length (about 16 rows or more).  A segment streams
-// rows beyond its own (2 whose populations cross its ends, and 2R that only
-// fill the y window, at a fraction of a row's cost), and a launch ends with
-// a tail while its last CTAs finish.  With w = items / resident CTAs (the
-// waves) the step time follows
-//   (segment rows + c) (w + a),
-// c = 0.5 + 2R extra rows (2 for LW-ACM, R = 0) and a = 0.2 of an item's
-// time, except for LW-ACM with FP32 storage, which runs near the memory
-// bound and whose extra rows mostly come from L2: c = 0.5, a = 0.4.  This
-// fits, within
-// 1.3 %, step times measured on GB300 over segment counts (FD-5 on 4096^2,
-// 8192^2 and 16384^2; FD-3, LW-ACM and LW-ACM with FP16 storage on 8192^2).
-// The minimum lies at 3-7 waves for the finite-difference steps on the large
-// lattices (8192^2 FD-5: 128 segments of 64 rows, 206 GLUPS, against 192 for
-// one wave of 241-row segments) and at 16-row segments for LW-ACM (275
-// GLUPS against 243 for 119-row segments).
-Plan make_plan(int nx, int ny, int R, int W, int resident_ctas, int elem_bytes) {
+// Row segments.  A segment streams rows beyond its own (2 whose populations
+// cross its ends, and 2R that only fill the y window, at a fraction of a
+// row's cost), and a launch ends with a tail while its last CTAs finish.
+// With w = items / resident CTAs (the waves), a plan of equal segments takes
+//   (segment rows + c) (w + a)
+// row-times of one resident CTA, c = 0.5 + 2R extra rows (2 for LW-ACM,
+// R = 0) and a = 0.2 of an item's time, except for LW-ACM with FP32 storage,
+// which runs near the memory bound and whose extra rows mostly come from L2:
+// c = 0.5, a = 0.4.  This fits, within 1.3 %, step times measured on GB300
+// over segment counts (FD-5 on 4096^2, 8192^2 and 16384^2; FD-3, LW-ACM and
+// LW-ACM with FP16 storage on 8192^2).
+//
+// The finite-difference steps do better with two segment lengths: nsegs long
+// segments of seg_rows rows per strip, then the remaining rows in short
+// segments of tail_rows, the long ones first in the item order.  The long
+// items cut the extra rows; the short ones, taken by whichever CTAs finish
+// first, absorb the spread of the long items' finishing times and leave a
+// short tail.  Such a plan takes
+//   strips (nsegs (seg_rows + c) + ntail (tail_rows + c)) / resident + a (tail_rows + c)
+// provided the short items give every resident CTA at least kSpread long
+// items' worth of work, the spread (the largest seg_rows meeting it is taken;
+// otherwise long segments finishing late set the step time).
+// Measured on 8192^2 FD-5 (GLUPS): equal 64-row segments 205.1, 34 segments
+// of 200 rows then 32-row ones 213.7; 16384^2: equal 120-row segments 221.7,
+// 35 of 400 then 48 rows 229.0.  LW-ACM is slower with long segments (8192^2:
+// 275.0 with equal 16-row segments, 230.7 with 34 of 200 then 16) and keeps
+// equal ones.
+constexpr double kSpread = 0.22;
+constexpr int kTailRows[] = {16, 24, 32, 48, 64};
+
+struct PlanModel {
+    double P, S, c, a;
+    bool two_size;  // the finite-difference steps
+};
+
+PlanModel plan_model(int nx, int R, int W, int resident_ctas, int elem_bytes) {
     const int nstrips = (nx + kStrip - 1) / kStrip;
-    Plan best{W, (nstrips + W - 1) / W, ny, 1, 0, 0};
     const bool near_memory_bound = R == 0 && elem_bytes == 4;
-    const double c = near_memory_bound ? 0.5 : (R == 0 ? 2.0 : 0.5 + 2.0 * R);
-    const double a = near_memory_bound ? 0.4 : 0.2;
-    double best_cost = -1.0;
+    PlanModel m;
+    m.P = (nstrips + W - 1) / W;
+    m.S = resident_ctas;
+    m.c = near_memory_bound ? 0.5 : (R == 0 ? 2.0 : 0.5 + 2.0 * R);
+    m.a = near_memory_bound ? 0.4 : 0.2;
+    m.two_size = R > 0;
+    return m;
+}
+
+// Step time of a plan in row-times of one resident CTA (see above); the
+// spread condition is not part of it.
+double plan_cost(const PlanModel& m, int ny, int B, int nb, int t) {
+    if (nb * B >= ny) {  // equal segments
+        const int n = (ny + B - 1) / B;
+        return (B + m.c) * (m.P * n / m.S + m.a);
+    }
+    const int nt = (ny - nb * B + t - 1) / t;
+    return m.P * (nb * (B + m.c) + nt * (t + m.c)) / m.S + m.a * (t + m.c);
+}
+
+bool covers_spread(const PlanModel& m, int ny, int B, int nb, int t) {
+    const int nt = (ny - nb * B + t - 1) / t;
+    return m.P * nt * (t + m.c) / m.S >= kSpread * (B + m.c);
+}
+
+struct PlanChoice {
+    double cost;
+    int B, nb, t;  // equal segments: nb * B >= ny, t = B
+};
+
+// Longest first segments (a multiple of 8 rows, at least twice the tail's,
+// leaving a tail) of nb per strip whose tail gives every resident CTA at
+// least `spread` of a first segment's work; 0 if none.
+int longest_first(const PlanModel& m, int ny, int nb, int t, double spread) {
+    if (nb * 2 * t >= ny) return 0;
+    for (int B = ((ny - t) / nb) & ~7; B >= 2 * t; B -= 8) {
+        const int nt = (ny - nb * B + t - 1) / t;
+        if (m.P * nt * (t + m.c) / m.S >= spread * (B + m.c)) return B;
+    }
+    return 0;
+}
+
+// Candidate plans, the model's first, then the rest cheapest first by the
+// model.  Equal segments: the two cheapest segment counts.  Two lengths
+// (finite differences only): a first part of about k waves, k = 1, 2, 3
+// (nsegs = k resident / strips), then tail_rows from kTailRows, with the
+// longest first segments whose tail covers kSpread of their work (the model's
+// choice among these is the cheapest), the lengths 8 rows either side of it,
+// and those covering 0.3 and 0.4 (for measurement).
+std::vector<PlanChoice> plan_candidates(int nx, int ny, int R, int W, int resident_ctas,
+                                        int elem_bytes) {
+    const PlanModel m = plan_model(nx, R, W, resident_ctas, elem_bytes);
+    std::vector<PlanChoice> eq, rest;
     const int max_segs = (ny + 15) / 16;
     for (int n = 1; n <= max_segs; ++n) {
         const int s = (ny + n - 1) / n;
-        const int nsegs = (ny + s - 1) / s;
-        if (nsegs != n) continue;  // the same segments as a smaller count
-        const double waves = (double)best.ncstrips * nsegs / resident_ctas;
-        const double cost = (s + c) * (waves + a);
-        if (best_cost < 0.0 || cost < best_cost) {
-            best_cost = cost;
-            best.seg_rows = s;
-            best.nsegs = nsegs;
+        if ((ny + s - 1) / s != n) continue;  // the same segments as a smaller count
+        eq.push_back({plan_cost(m, ny, s, n, s), s, n, s});
+    }
+    const auto cheaper = [](const PlanChoice& x, const PlanChoice& y) { return x.cost < y.cost; };
+    std::sort(eq.begin(), eq.end(), cheaper);
+    if (eq.size() > 2) eq.resize(2);
+    PlanChoice pick = eq[0];
+    rest = eq;
+    if (m.two_size) {
+        for (int k = 1; k <= 3; ++k) {
+            const int nb = (int)(k * m.S / m.P);
+            if (nb < 1) continue;
+            for (const int t : kTailRows) {
+                const int B = longest_first(m, ny, nb, t, kSpread);
+                if (B == 0) continue;
+                const PlanChoice pc{plan_cost(m, ny, B, nb, t), B, nb, t};
+                if (pc.cost < pick.cost) pick = pc;
+                for (const int b : {B - 8, B, B + 8, longest_first(m, ny, nb, t, 0.3),
+                                    longest_first(m, ny, nb, t, 0.4)}) {
+                    if (b < 2 * t || nb * b > ny - t) continue;
+                    bool seen = false;
+                    for (const PlanChoice& q : rest) seen |= q.B == b && q.nb == nb && q.t == t;
+                    if (!seen) rest.push_back({plan_cost(m, ny, b, nb, t), b, nb, t});
+                }
+            }
         }
     }
-    best.nitems = best.ncstrips * best.nsegs;
-    best.blocks = best.nitems;
-    return best;
+    std::sort(rest.begin(), rest.end(), cheaper);
+    std::vector<PlanChoice> out{pick};
+    for (const PlanChoice& pc : rest)
+        if (pc.B != pick.B || pc.nb != pick.nb || pc.t != pick.t) out.push_back(pc);
+    return out;
+}
+
+// The launch plan for segments (B, nb, t): nb segments of B rows, then the
+// rest in segments of t rows; nb * B >= ny means equal segments of B rows.
+Plan plan_of(int nx, int ny, int W, int B, int nb, int t) {
+    const int nstrips = (nx + kStrip - 1) / kStrip;
+    Plan p;
+    p.W = W;
+    p.ncstrips = (nstrips + W - 1) / W;
+    if (nb * B >= ny) {
+        p.seg_rows = p.tail_rows = B;
+        p.nsegs = (ny + B - 1) / B;
+        p.ntail = 0;
+    } else {
+        p.seg_rows = B;
+        p.nsegs = nb;
+        p.tail_rows = t;
+        p.ntail = (ny - nb * B + t - 1) / t;
+    }
+    p.nitems = p.ncstrips * (p.nsegs + p.ntail);
+    p.blocks = p.nitems;
+    return p;
+}
+
+Plan make_plan(int nx, int ny, int R, int W, int resident_ctas, int elem_bytes) {
+    const PlanChoice pc = plan_candidates(nx, ny, R, W, resident_ctas, elem_bytes)[0];
+    return plan_of(nx, ny, W, pc.B, pc.nb, pc.t);
+}
+
+void store_plan(fdlbm_s* h, const Plan& pl) {
+    const int v[6] = {pl.seg_rows, pl.nsegs, pl.tail_rows, pl.ntail, pl.ncstrips, pl.nitems};
+    std::copy(v, v + 6, h->stream_plan);
+}
+
+Plan cached_plan(const fdlbm_s* h, int W) {
+    Plan p;
+    p.W = W;
+    p.seg_rows = h->stream_plan[0];
+    p.nsegs = h->stream_plan[1];
+    p.tail_rows = h->stream_plan[2];
+    p.ntail = h->stream_plan[3];
+    p.ncstrips = h->stream_plan[4];
+    p.nitems = p.blocks = h->stream_plan[5];
+    return p;
+}
+
+int stencil_radius(int32_t scheme) {
+    switch (scheme) {
+        case FDLBM_SCHEME_FD3: return 1;
+        case FDLBM_SCHEME_FD5: return 2;
+        case FDLBM_SCHEME_LWACM: return 0;
+        default: return -1;
+    }
+}
+
+int storage_bytes(int32_t storage) {
+    switch (storage) {
+        case FDLBM_STORAGE_F32: return 4;
+        case FDLBM_STORAGE_F16:
+        case FDLBM_STORAGE_BF16:
+        case FDLBM_STORAGE_I16: return 2;
+        default: return 0;
+    }
 }
 
 template <int R, bool FORCE, bool WALLS, typename T, int W>
@@ -476,8 +633,12 @@ cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, W * 32, smem);
         h->stream_plan_warps = std::max(1, sms * per_sm);  // resident CTAs
+        if (!h->stream_plan_user) {
+            const Plan pl = make_plan(h->p.nx, h->p.ny, R, W, h->stream_plan_warps, (int)sizeof(T));
+            store_plan(h, pl);
+        }
     }
-    const Plan plan = make_plan(h->p.nx, h->p.ny, R, W, h->stream_plan_warps, (int)sizeof(T));
+    const Plan plan = cached_plan(h, W);
     StreamArgs a;
     a.src = src;
     a.dst = dst;
@@ -490,6 +651,7 @@ cudaError_t launch_stream_w(fdlbm_s* h, const void* src, void* dst) {
     a.ncstrips = plan.ncstrips;
     a.seg_rows = plan.seg_rows;
     a.nsegs = plan.nsegs;
+    a.tail_rows = plan.tail_rows;
     a.nitems = plan.nitems;
     const double sc = (R == 1) ? 0.5 : 0.125;  // derivatives are computed times 2 or 8
     const double ae = (1.0 - 1.0 / h->p.s_e) * sc / 36.0;
@@ -553,26 +715,64 @@ cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst) {
 extern "C" int fdlbm_stream_plan(int32_t nx, int32_t ny, int32_t scheme, int32_t storage,
                                  int32_t resident_ctas, int32_t* plan) {
     using namespace fdlbm;
-    if (!plan || nx < 1 || ny < 1 || resident_ctas < 1) return FDLBM_ERR_INVALID;
-    int R;
-    switch (scheme) {
-        case FDLBM_SCHEME_FD3: R = 1; break;
-        case FDLBM_SCHEME_FD5: R = 2; break;
-        case FDLBM_SCHEME_LWACM: R = 0; break;
-        default: return FDLBM_ERR_INVALID;
-    }
-    int elem;
-    switch (storage) {
-        case FDLBM_STORAGE_F32: elem = 4; break;
-        case FDLBM_STORAGE_F16:
-        case FDLBM_STORAGE_BF16:
-        case FDLBM_STORAGE_I16: elem = 2; break;
-        default: return FDLBM_ERR_INVALID;
-    }
+    const int R = stencil_radius(scheme), elem = storage_bytes(storage);
+    if (!plan || nx < 1 || ny < 1 || resident_ctas < 1 || R < 0 || elem == 0)
+        return FDLBM_ERR_INVALID;
     const Plan p = make_plan(nx, ny, R, kWarps, resident_ctas, elem);
     plan[0] = p.seg_rows;
     plan[1] = p.nsegs;
-    plan[2] = p.ncstrips;
-    plan[3] = p.nitems;
+    plan[2] = p.tail_rows;
+    plan[3] = p.ntail;
+    plan[4] = p.ncstrips;
+    plan[5] = p.nitems;
+    return FDLBM_OK;
+}
+
+extern "C" int fdlbm_stream_plan_candidates(int32_t nx, int32_t ny, int32_t scheme,
+                                            int32_t storage, int32_t resident_ctas,
+                                            int32_t* out, int32_t max, int32_t* count) {
+    using namespace fdlbm;
+    const int R = stencil_radius(scheme), elem = storage_bytes(storage);
+    if (!out || !count || max < 1 || nx < 1 || ny < 1 || resident_ctas < 1 || R < 0 ||
+        elem == 0)
+        return FDLBM_ERR_INVALID;
+    const std::vector<PlanChoice> c = plan_candidates(nx, ny, R, kWarps, resident_ctas, elem);
+    const int n = std::min<int>(max, (int)c.size());
+    for (int i = 0; i < n; ++i) {
+        out[3 * i] = c[i].B;
+        out[3 * i + 1] = c[i].nb * c[i].B >= ny ? (ny + c[i].B - 1) / c[i].B : c[i].nb;
+        out[3 * i + 2] = c[i].t;
+    }
+    *count = n;
+    return FDLBM_OK;
+}
+
+extern "C" int fdlbm_set_stream_plan(fdlbm_t* h, int32_t seg_rows, int32_t nsegs,
+                                     int32_t tail_rows) {
+    using namespace fdlbm;
+    if (!h) return FDLBM_ERR_INVALID;
+    if (!uses_stream_step(h)) return FDLBM_ERR_INVALID;
+    const int ny = h->p.ny;
+    if (seg_rows == 0 && nsegs == 0 && tail_rows == 0) {  // back to the model's plan
+        h->stream_plan_user = 0;
+        if (h->stream_plan_warps > 0)
+            store_plan(h, make_plan(h->p.nx, ny, stencil_radius(h->p.scheme), kWarps,
+                                    h->stream_plan_warps, storage_bytes(h->p.storage)));
+        return FDLBM_OK;
+    }
+    if (seg_rows < 1 || nsegs < 1 || tail_rows < 1 || seg_rows > ny) return FDLBM_ERR_INVALID;
+    // equal segments when the first part reaches the last row
+    if ((int64_t)seg_rows * nsegs >= ny) nsegs = (ny + seg_rows - 1) / seg_rows;
+    store_plan(h, plan_of(h->p.nx, ny, kWarps, seg_rows, nsegs, tail_rows));
+    h->stream_plan_user = 1;
+    return FDLBM_OK;
+}
+
+extern "C" int fdlbm_get_stream_plan(fdlbm_t* h, int32_t* plan) {
+    using namespace fdlbm;
+    if (!h || !plan || !uses_stream_step(h) || h->stream_plan_warps < 1)
+        return FDLBM_ERR_INVALID;
+    std::copy(h->stream_plan, h->stream_plan + 6, plan);
+    plan[6] = h->stream_plan_warps;
     return FDLBM_OK;
 }

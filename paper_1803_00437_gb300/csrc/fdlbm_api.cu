@@ -220,6 +220,7 @@ int fdlbm_create(const fdlbm_params* p, void* workspace, size_t bytes, void* str
     h->cur = 0;
     h->launches = 0;
     h->stream_plan_warps = 0;
+    h->stream_plan_user = 0;
     h->fd_path = (p->flags & FDLBM_FLAG_TILED) ? 1 : (p->flags & FDLBM_FLAG_STREAM) ? 2 : 0;
     h->err[0] = 0;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -486,13 +487,16 @@ int64_t fdlbm_launch_count(const fdlbm_t* h) { return h ? h->launches : -1; }
 }  // extern "C"
 
 namespace fdlbm {
-cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
+bool uses_stream_step(const fdlbm_s* h) {
     // the streaming kernel pays off once the lattice fills the GPU's warps
     constexpr int64_t kStreamMinNodes = 1 << 20;
     const bool big = (int64_t)h->p.nx * h->p.ny >= kStreamMinNodes;
-    if (h->p.scheme != FDLBM_SCHEME_FD9 && h->fd_path != 1 && fd_stream_supported(h->p) &&
-        (big || h->fd_path == 2))
-        return launch_fd_step_stream(h, src, dst);
+    return h->p.scheme != FDLBM_SCHEME_MRT && h->p.scheme != FDLBM_SCHEME_FD9 &&
+           h->fd_path != 1 && fd_stream_supported(h->p) && (big || h->fd_path == 2);
+}
+
+cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst) {
+    if (uses_stream_step(h)) return launch_fd_step_stream(h, src, dst);
     return launch_fd_step_tiled(h, src, dst);
 }
 }  // namespace fdlbm

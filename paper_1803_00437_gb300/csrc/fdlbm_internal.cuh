@@ -161,7 +161,9 @@ struct fdlbm_s {
     char* ws;
     int cur;  // index of the current state copy
     int64_t launches;
-    int stream_plan_warps;  // resident warps of the streaming FD kernel (0: not queried)
+    int stream_plan_warps;  // resident CTAs of the streaming FD kernel (0: not queried)
+    int stream_plan[6];     // its launch plan (see make_plan)
+    int stream_plan_user;   // 1: the plan was set by fdlbm_set_stream_plan
     int fd_path;            // 0: automatic, 1: tiled FD kernel, 2: streaming where it qualifies
     const void* walls;      // curved walls: device table of closure entries (NULL: none)
     int64_t walls_n;        // its number of entries
@@ -183,6 +185,7 @@ MrtCoeffs mrt_coeffs(const fdlbm_params& p);
 cudaError_t launch_fd_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_step_tiled(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_step_stream(fdlbm_s* h, const void* src, void* dst);
+bool uses_stream_step(const fdlbm_s* h);
 bool fd_stream_supported(const fdlbm_params& p);
 cudaError_t launch_mrt_step(fdlbm_s* h, const void* src, void* dst);
 cudaError_t launch_fd_init(fdlbm_s* h, const float* drho, const float* ux, const float* uy,

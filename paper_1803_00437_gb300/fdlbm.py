@@ -116,6 +116,13 @@ def load_library(path: str | None = None):
         L.fdlbm_batch_set_narrow_strips.argtypes = [vp, i32]
         L.fdlbm_stream_plan.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32)]
         L.fdlbm_stream_plan.restype = ctypes.c_int
+        L.fdlbm_stream_plan_candidates.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32),
+                                                   i32, ctypes.POINTER(i32)]
+        L.fdlbm_stream_plan_candidates.restype = ctypes.c_int
+        L.fdlbm_set_stream_plan.argtypes = [vp, i32, i32, i32]
+        L.fdlbm_set_stream_plan.restype = ctypes.c_int
+        L.fdlbm_get_stream_plan.argtypes = [vp, ctypes.POINTER(i32)]
+        L.fdlbm_get_stream_plan.restype = ctypes.c_int
         L.fdlbm_batch_last_error.argtypes = [vp]
         L.fdlbm_batch_last_error.restype = cp
         L.fdlbm_batch_launch_count.argtypes = [vp]
@@ -154,15 +161,34 @@ def status_string(status: int) -> str:
 
 def stream_plan(nx: int, ny: int, scheme: str = "fd5", storage: str = "f32",
                 resident_ctas: int = 152 * 8) -> dict:
-    """The streaming step's launch plan (fdlbm_stream_plan): rows per segment,
-    segments, CTA strips and CTAs for an nx x ny lattice; host-only."""
+    """The streaming step's launch plan (fdlbm_stream_plan) for an nx x ny
+    lattice: rows per long segment and their number, rows per short segment
+    and their number (0 if all segments are equal), CTA strips and CTAs;
+    host-only."""
     lib = load_library()
-    out = (ctypes.c_int32 * 4)()
+    out = (ctypes.c_int32 * 6)()
     rc = lib.fdlbm_stream_plan(int(nx), int(ny), SCHEMES[scheme], STORAGES[storage],
                                int(resident_ctas), out)
     if rc != OK:
         raise FdlbmError(rc, f"stream plan: {status_string(rc)}")
-    return {"seg_rows": out[0], "nsegs": out[1], "strips": out[2], "ctas": out[3]}
+    return {"seg_rows": out[0], "nsegs": out[1], "tail_rows": out[2], "ntail": out[3],
+            "strips": out[4], "ctas": out[5]}
+
+
+def stream_plan_candidates(nx: int, ny: int, scheme: str = "fd5", storage: str = "f32",
+                           resident_ctas: int = 152 * 8, max_candidates: int = 32) -> list:
+    """Candidate plans of the streaming step (fdlbm_stream_plan_candidates):
+    (rows per long segment, long segments, rows per short segment) tuples,
+    the model's plan first; host-only."""
+    lib = load_library()
+    out = (ctypes.c_int32 * (3 * max_candidates))()
+    n = ctypes.c_int32()
+    rc = lib.fdlbm_stream_plan_candidates(int(nx), int(ny), SCHEMES[scheme], STORAGES[storage],
+                                          int(resident_ctas), out, int(max_candidates),
+                                          ctypes.byref(n))
+    if rc != OK:
+        raise FdlbmError(rc, f"stream plan candidates: {status_string(rc)}")
+    return [(out[3 * i], out[3 * i + 1], out[3 * i + 2]) for i in range(n.value)]
 
 
 def nu_to_s(nu: float) -> float:
@@ -381,6 +407,66 @@ class Lattice:
     @property
     def launches(self) -> int:
         return int(self.lib.fdlbm_launch_count(self._h))
+
+    def set_stream_plan(self, seg_rows: int = 0, nsegs: int = 0, tail_rows: int = 0):
+        """Row segments of the streaming step (fdlbm_set_stream_plan); no
+        arguments: back to the model's plan."""
+        self._check(self.lib.fdlbm_set_stream_plan(self._h, int(seg_rows), int(nsegs),
+                                                   int(tail_rows)), "set_stream_plan")
+
+    def stream_plan(self):
+        """The streaming step's plan in use (fdlbm_get_stream_plan) as a dict,
+        or None if the lattice has not stepped or does not stream."""
+        out = (ctypes.c_int32 * 7)()
+        if self.lib.fdlbm_get_stream_plan(self._h, out) != OK:
+            return None
+        return {"seg_rows": out[0], "nsegs": out[1], "tail_rows": out[2], "ntail": out[3],
+                "strips": out[4], "ctas": out[5], "resident_ctas": out[6]}
+
+    _tuned: dict = {}
+
+    def tune(self, steps: int = 10, max_candidates: int = 32):
+        """Autotuner over the streaming step's row segments: times `steps`
+        steps under each candidate plan of fdlbm_stream_plan_candidates,
+        keeps the fastest (cached per device, size, scheme, storage and
+        boundary) and returns it as (seg_rows, nsegs, tail_rows) with the
+        timings in milliseconds per step; None for a lattice that does not
+        run on the streaming kernel.  The lattice's state is saved before and
+        restored after (the moments are the whole FD-LBM state), so tuning
+        does not advance it."""
+        import torch
+        cfg = self.cfg
+        key = (torch.cuda.get_device_name(self.device), cfg.nx, cfg.ny, cfg.scheme,
+               cfg.storage, cfg.boundary)
+        if key in Lattice._tuned:
+            best, timings = Lattice._tuned[key]
+            self.set_stream_plan(*best)
+            return best, timings
+        saved = [t.clone() for t in self.moments()]
+        self.step(1)
+        plan = self.stream_plan()
+        if plan is None:
+            self.init(*saved)
+            return None
+        cands = stream_plan_candidates(cfg.nx, cfg.ny, cfg.scheme, cfg.storage,
+                                       plan["resident_ctas"], max_candidates)
+        timings = {}
+        for cand in cands:
+            self.set_stream_plan(*cand)
+            self.step(2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            self.step(steps)
+            e1.record(self.stream)
+            self.sync()
+            timings[cand] = e0.elapsed_time(e1) / steps
+        best = min(timings, key=timings.get)
+        Lattice._tuned[key] = (best, timings)
+        self.set_stream_plan(*best)
+        self.init(*saved)
+        self.sync()
+        return best, timings
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
