@@ -417,8 +417,14 @@ __device__ __forceinline__ void stream_row(const float2 nr[2], const float2 nux[
         G[q][3] = g[1][q].y;
     }
     float ss_[4], ds_[4], su_[4], du_[4], sd_[4], dd_[4];
+    // columns 1 and 2 take their neighbours' populations from whole pairs
+    // ((G1[0], G1[1]) = g[0][1], (G3[2], G3[3]) = g[1][3], and so on): one
+    // paired instruction for two scalar ones, each sum rounded as before
+    const float2 p13 = add2(g[0][1], g[1][3]), m13 = sub2(g[0][1], g[1][3]);
+    const float2 p56 = add2(g[0][5], g[1][6]), m56 = sub2(g[0][5], g[1][6]);
+    const float2 p78 = add2(g[1][7], g[0][8]), m87 = sub2(g[0][8], g[1][7]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 4; j += 3) {
         const float q1 = j ? G[1][j - 1] : in1, q5 = j ? G[5][j - 1] : in5;
         const float q8 = j ? G[8][j - 1] : in8;
         const float q3 = j < 3 ? G[3][j + 1] : in3, q6 = j < 3 ? G[6][j + 1] : in6;
@@ -430,6 +436,18 @@ __device__ __forceinline__ void stream_row(const float2 nr[2], const float2 nux[
         sd_[j] = G[4][j] + (q7 + q8);
         dd_[j] = q8 - q7;
     }
+    ss_[1] = G[0][1] + p13.x;
+    ss_[2] = G[0][2] + p13.y;
+    ds_[1] = m13.x;
+    ds_[2] = m13.y;
+    su_[1] = G[2][1] + p56.x;
+    su_[2] = G[2][2] + p56.y;
+    du_[1] = m56.x;
+    du_[2] = m56.y;
+    sd_[1] = G[4][1] + p78.x;
+    sd_[2] = G[4][2] + p78.y;
+    dd_[1] = m87.x;
+    dd_[2] = m87.y;
 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

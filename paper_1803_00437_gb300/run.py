@@ -25,6 +25,12 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=0, help="untimed steps before the timed ones")
     ap.add_argument("--per-step", action="store_true",
                     help="one fdlbm_step call per step")
+    ap.add_argument("--plan", default=None,
+                    help="row segments of the streaming step, SEG_ROWS,NSEGS,TAIL_ROWS "
+                         "(fdlbm_set_stream_plan)")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the streaming step's candidate plans first and keep the "
+                         "fastest (Lattice.tune; the state is restored)")
     ap.add_argument("--nu", type=float, default=0.01)
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--reduce", nargs="*", default=[],
@@ -39,6 +45,10 @@ def main(argv=None):
     lat = F.Lattice(F.LatticeConfig(n, n, args.scheme, s_xx=F.nu_to_s(args.nu), s_e=1.5,
                                     storage=args.storage, storage_range=args.range))
     lat.init_modes(inputs.random_modes(n, n, args.modes, 1e-3, seed=inputs.seed_for(1)))
+    if args.plan:
+        lat.set_stream_plan(*[int(v) for v in args.plan.split(",")])
+    if args.tune:
+        lat.tune()
     lat.step(args.warmup)
     lat.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -55,6 +65,7 @@ def main(argv=None):
     print(json.dumps({"side": n, "scheme": args.scheme, "storage": args.storage,
                       "steps": args.steps, "ms_per_step": round(ms, 4),
                       "mlups": round(n * n / ms / 1e3, 1), "launches": lat.launches,
+                      "stream_plan": lat.stream_plan(),
                       "max_u": float(lat.reduce("maxabs")[0]), "reductions": reductions}))
 
 
