@@ -93,3 +93,28 @@ def test_saturation_is_reported(flags):
     with pytest.raises(F.FdlbmError) as e:
         ch.sync()
     assert e.value.status == F.ERR_RANGE
+
+
+@pytest.mark.parametrize("flags", [1, 2])
+def test_step_saturates_symmetrically(flags):
+    """Values a step carries past the range are stored as +-32767 steps
+    (never -32768) by both FD-LBM kernels: channels driven upward and
+    downward past a range of 2e-3 end with max |ux| equal to it."""
+    import torch
+    from paper_1803_00437_gb300 import fdlbm as F
+    scale = np.float32(2e-3 / 32767.0)
+    top = np.float32(scale * np.float32(32767))
+    for fx in (1e-5, -1e-5):
+        ch = F.Lattice(_cfg(256, 32, "fd5", 2e-3, flags=flags, boundary="walls_y",
+                            wall_xi=0.5, force=(fx, 0.0)))
+        z = torch.zeros((32, 256), dtype=torch.float32, device="cuda")
+        ch.init(z, z, z)
+        ch.step(400)
+        with pytest.raises(F.FdlbmError):
+            ch.sync()
+        ux = ch.moments()[1].cpu().numpy()
+        ch.sync()
+        assert np.abs(ux).max() == top
+        assert (ux.max() if fx > 0 else -ux.min()) == top
+        q = np.rint(ux / scale)
+        assert np.abs(q).max() <= 32767 and np.array_equal(q.astype(np.float32) * scale, ux)
