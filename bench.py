@@ -59,8 +59,8 @@ def parse_args():
                     help="throughput: the 8192^2 headline line (default); batched: 4096 "
                          "lattices of sides 32..512; serving: the request stream")
     ap.add_argument("--lattices", type=int, default=4096, help=argparse.SUPPRESS)
-    ap.add_argument("--batched-lattices", type=int, default=1024,
-                    help="lattices of the batched sample in the default line")
+    ap.add_argument("--batched-lattices", type=int, default=4096,
+                    help="lattices of the batched workload in the default line (all 4096 of it)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=300,
                     help="requests of the serving sample in the default line")

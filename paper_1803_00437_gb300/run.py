@@ -32,6 +32,9 @@ def main(argv=None):
                     help="time the streaming step's candidate plans first and keep the "
                          "fastest (Lattice.tune; the state is restored)")
     ap.add_argument("--nu", type=float, default=0.01)
+    ap.add_argument("--walls", type=float, default=None, metavar="XI",
+                    help="a channel: walls in y at offset XI (Sec. 3-b), periodic in x")
+    ap.add_argument("--force", type=float, default=0.0, help="body force along x (channels)")
     ap.add_argument("--modes", type=int, default=32)
     ap.add_argument("--reduce", nargs="*", default=[],
                     choices=["mass", "momentum", "energy", "maxabs"],
@@ -42,8 +45,10 @@ def main(argv=None):
     from . import build, fdlbm as F, inputs
     build.build()
     n = args.side
+    walls = {} if args.walls is None else dict(boundary="walls_y", wall_xi=args.walls,
+                                               force=(args.force, 0.0))
     lat = F.Lattice(F.LatticeConfig(n, n, args.scheme, s_xx=F.nu_to_s(args.nu), s_e=1.5,
-                                    storage=args.storage, storage_range=args.range))
+                                    storage=args.storage, storage_range=args.range, **walls))
     lat.init_modes(inputs.random_modes(n, n, args.modes, 1e-3, seed=inputs.seed_for(1)))
     if args.plan:
         lat.set_stream_plan(*[int(v) for v in args.plan.split(",")])
@@ -63,6 +68,7 @@ def main(argv=None):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     reductions = {w: [float(v) for v in lat.reduce(w)] for w in args.reduce}
     print(json.dumps({"side": n, "scheme": args.scheme, "storage": args.storage,
+                      "boundary": "periodic" if args.walls is None else f"walls_y xi={args.walls}",
                       "steps": args.steps, "ms_per_step": round(ms, 4),
                       "mlups": round(n * n / ms / 1e3, 1), "launches": lat.launches,
                       "stream_plan": lat.stream_plan(),
