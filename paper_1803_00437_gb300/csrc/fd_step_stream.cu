@@ -447,14 +447,17 @@ constexpr int kWarps = 2;
 // first, absorb the spread of the long items' finishing times and leave a
 // short tail.  Such a plan takes
 //   strips (nsegs (seg_rows + c) + ntail (tail_rows + c)) / resident + a (tail_rows + c)
-// provided the short items give every resident CTA at least kSpread long
-// items' worth of work, the spread (the largest seg_rows meeting it is taken;
-// otherwise long segments finishing late set the step time).
-// Measured on 8192^2 FD-5 (GLUPS): equal 64-row segments 205.1, 34 segments
-// of 200 rows then 32-row ones 213.7; 16384^2: equal 120-row segments 221.7,
-// 35 of 400 then 48 rows 229.0.  LW-ACM is slower with long segments (8192^2:
-// 275.0 with equal 16-row segments, 230.7 with 34 of 200 then 16) and keeps
-// equal ones.
+// provided the short items give every resident CTA at least kSpread of a
+// long item's work, the spread of the long items' finishing times (the
+// largest seg_rows meeting it is taken; otherwise long segments finishing
+// late set the step time).  Measured on 8192^2 FD-5 (GLUPS): equal 64-row
+// segments 205.1, 34 segments of 200 rows then 32-row ones 213.7; 16384^2:
+// equal 120-row segments 221.7, 35 of 400 then 48 rows 229.0.  Near the
+// optimum the step times vary by 1-2 % from one plan to the next in ways the
+// model does not follow, so plan_candidates also lists the neighbouring plans
+// for measurement on the device.  LW-ACM is slower with long segments
+// (8192^2: 275.0 with equal 16-row segments, 230.7 with 34 of 200 then 16)
+// and keeps equal ones.
 constexpr double kSpread = 0.22;
 constexpr int kTailRows[] = {16, 24, 32, 48, 64};
 
